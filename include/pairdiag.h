@@ -1,0 +1,208 @@
+/*
+ * pairdiag.h -- C ABI of the GB300 (sm_103a) ground-state solver for the
+ * general pairing Hamiltonian in the seniority-zero pair basis.
+ *
+ *   H = sum_i (2 e_i + G_ii) n_i + sum_{i != j} G_ij P_i^+ P_j          (Eq. 2)
+ *
+ * Omega orbits (1 <= Omega <= 62), N pairs (0 <= N <= Omega).  A basis state
+ * is an Omega-bit word with N set bits, bit p = orbit p (Sec. 3.1); basis
+ * index r (0-based) is the state's position in ascending integer order, i.e.
+ * the paper's hash value minus one (Sec. 3.2).  All vectors exchanged through
+ * this ABI are in that order.
+ *
+ * Conventions for every entry point:
+ *   - return value: PD_OK (0) on success, a negative PD_E* code otherwise;
+ *     pairdiag_last_error() gives a one-line description of the last failure
+ *     on the calling thread.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the handle's device (for example torch tensors'
+ *     data_ptr()).  Nothing is retained after a call returns except what the
+ *     handle owns.
+ *   - kernels run on the handle's stream (pairdiag_set_stream; default: the
+ *     legacy default stream).  Entry points taking host buffers synchronise
+ *     that stream before returning; the *_dev entry points are asynchronous
+ *     unless stated.
+ *   - inputs are copied at create time; the caller keeps ownership of every
+ *     buffer it passes.  The handle owns its device memory (basis tables,
+ *     Lanczos window) and frees it in pairdiag_destroy.
+ */
+#ifndef PAIRDIAG_H
+#define PAIRDIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status ---- */
+#define PD_OK        0
+#define PD_EINVAL   -1   /* bad argument: Omega/N out of range, G not symmetric, non-finite input */
+#define PD_ENOMEM   -2   /* device memory exhausted (dimension x window too large) */
+#define PD_ENOCONV  -3   /* tolerance not reached in max_restarts; best estimate still returned */
+#define PD_ETIMEOUT -4   /* a bounded device-side wait expired */
+#define PD_ECUDA    -5   /* a CUDA runtime error */
+#define PD_ENOTSUP  -6   /* request outside what this build supports */
+
+/* precision of the Lanczos vectors and of H*x */
+#define PD_PREC_FP64  0  /* FP64 vectors, FP64 row accumulation */
+#define PD_PREC_MIXED 1  /* FP32 vectors + FP32 row sums; FP64 dots, FP64 tridiagonal
+                            solve and a final FP64 Rayleigh-quotient refinement */
+
+/* start vector of the first Lanczos cycle */
+#define PD_START_RANDOM 0  /* counter-based SplitMix64 uniform in [-1,1), seeded */
+#define PD_START_FIRST  1  /* [1,0,...,0]^T, the paper's default (Sec. 3.4) */
+#define PD_START_HF     2  /* unit vector on the state of lowest diagonal element */
+#define PD_START_USER   3  /* caller-provided vector (pairdiag_set_start) */
+
+typedef struct pairdiag pairdiag_t;   /* opaque; owned by the library */
+
+typedef struct {
+    int      window;        /* Lanczos vectors per cycle (the paper's Lanc_Limit, Sec. 4.1); default 20 */
+    int      max_restarts;  /* restart cycles before PD_ENOCONV; default 500 */
+    int      precision;     /* PD_PREC_FP64 or PD_PREC_MIXED; default PD_PREC_FP64 */
+    int      start;         /* PD_START_*; default PD_START_RANDOM */
+    uint64_t seed;          /* seed of PD_START_RANDOM; default 1 */
+    int      mode;          /* 0 = restarted Lanczos (the paper's Mode = 0), 1 = one Krylov
+                               space without restart (Mode = 1); default 0 */
+    int      low_bits;      /* orbits handled inside one basis block (0 = automatic) */
+    double   mixed_floor;   /* relative residual at which FP32 cycles hand over to FP64
+                               refinement (PD_PREC_MIXED only); default 5e-6 */
+} pairdiag_options;
+
+typedef struct {
+    int64_t dim;            /* C(Omega, N) */
+    int64_t nnz_offdiag;    /* C(Omega,N) * N * (Omega - N) off-diagonal elements (Sec. 5.3) */
+    int     iterations;     /* H*x products inside Lanczos (all precisions) */
+    int     iterations_fp32;/* of which with FP32 vectors */
+    int     restarts;       /* restart cycles */
+    int     converged;      /* 1 if |beta_1/alpha_1| <= tol was reached */
+    double  rel_residual;   /* ||Hv - E v|| / |E| of the returned vector (FP64) */
+    double  gap_estimate;   /* second minus lowest Ritz value of the last cycle */
+    double  seconds;        /* wall time of the call */
+} pairdiag_info;
+
+/* Fill *opt with the defaults listed above. */
+void pairdiag_default_options(pairdiag_options *opt);
+
+/* One-line description of a status code / of the last failure on this thread. */
+const char *pairdiag_strerror(int code);
+const char *pairdiag_last_error(void);
+
+/*
+ * Create a solver for Omega orbits and N pairs (the paper's N_Orbit, N_Pairs,
+ * SPE and P_F inputs, Sec. 4.1; Initialize(), App. B).
+ *   e : host, [omega] single-particle energies e_i
+ *   G : host, [omega*omega] row-major pairing strengths, G[i*omega+j] = V_ij;
+ *       must be exactly symmetric (the paper requires a real symmetric P_F).
+ *   opt: host, nullable (defaults).
+ *   out: receives the handle.
+ * Builds the block tables for the basis on the current CUDA device.
+ * Errors: PD_EINVAL (omega outside 1..62, N outside 0..omega, non-finite or
+ * asymmetric input), PD_ENOMEM, PD_ECUDA.
+ */
+int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
+                    const pairdiag_options *opt, pairdiag_t **out);
+
+/* Free every device and host resource of the handle (the paper's Destory()). */
+void pairdiag_destroy(pairdiag_t *h);
+
+/* Run the handle's kernels on this CUDA stream (cudaStream_t passed as void*). */
+int pairdiag_set_stream(pairdiag_t *h, void *stream);
+
+/* Dimension C(Omega,N) (Eq. extcmn) and off-diagonal count (Sec. 5.3). */
+int64_t pairdiag_dim(const pairdiag_t *h);
+int64_t pairdiag_nnz(const pairdiag_t *h);
+
+/*
+ * Basis states with indices [first, first+count) (Sec. 3.1, Table 1), written
+ * as uint64 words to out_dev (device, [count]).  Bit-exact.  Asynchronous.
+ */
+int pairdiag_basis_dev(const pairdiag_t *h, int64_t first, int64_t count, uint64_t *out_dev);
+
+/* The whole basis into host memory out (host, [dim]).  Synchronous. */
+int pairdiag_basis(const pairdiag_t *h, uint64_t *out);
+
+/*
+ * Index of each state (the hash of Sec. 3.2, 0-based): ranks_dev[i] = f(states_dev[i]) - 1.
+ * states_dev: device [count] Omega-bit words with N set bits (other words give
+ * UINT64_MAX).  Asynchronous.
+ */
+int pairdiag_rank_dev(const pairdiag_t *h, const uint64_t *states_dev, int64_t count,
+                      uint64_t *ranks_dev);
+
+/*
+ * y = H x computed on the fly (Sec. 3.3, Eq. diagonal), device buffers of dim
+ * elements in basis order.
+ *   precision PD_PREC_FP64: x_dev, y_dev are double; FP64 row sums.
+ *   precision PD_PREC_MIXED: x_dev, y_dev are float; FP32 row sums, G rounded to FP32.
+ * x_dev and y_dev must not overlap.  Asynchronous.
+ */
+int pairdiag_hx_dev(pairdiag_t *h, int precision, const void *x_dev, void *y_dev);
+
+/* y = H x in FP64 with host buffers x, y of dim doubles (copies included).  Synchronous. */
+int pairdiag_hx(pairdiag_t *h, const double *x, double *y);
+
+/*
+ * Monopole_Min, Monopole_Max and Posit_Min (Sec. 4.3, App. B): extreme
+ * diagonal elements and the lowest index attaining the minimum.  Synchronous.
+ */
+int pairdiag_monopole(pairdiag_t *h, double *dmin, double *dmax, int64_t *pos_min);
+
+/*
+ * Start vector for PD_START_USER: host [dim] doubles (copied).  Synchronous.
+ */
+int pairdiag_set_start(pairdiag_t *h, const double *v);
+
+/*
+ * Lowest eigenpair by restarted Lanczos (Algorithm 2 with full
+ * reorthogonalisation and restart, Sec. 3.4; the paper's Diag_Solver).
+ * Stops when |beta_1/alpha_1| <= tol (Sec. 5.1): the residual norm of the
+ * restart vector relative to its Rayleigh quotient.  PD_PREC_MIXED runs FP32
+ * cycles down to opt.mixed_floor, then FP64 Rayleigh refinement and, if
+ * needed, FP64 cycles.
+ *   e0  : host, receives the ground-state energy (Energy_Ground)
+ *   vec : host [dim] doubles, nullable: the normalised ground-state vector
+ *   info: host, nullable
+ * Returns PD_OK, or PD_ENOCONV with the best estimate filled in.  Synchronous.
+ */
+int pairdiag_ground_state(pairdiag_t *h, double tol, double *e0, double *vec,
+                          pairdiag_info *info);
+
+/* As pairdiag_ground_state, with the vector written to device memory
+ * (vec_dev: double [dim], nullable).  Synchronous (returns after E0 is known). */
+int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec_dev,
+                              pairdiag_info *info);
+
+/*
+ * Orbit occupation numbers 2 <v|S+_i S-_i|v> (N_Occup, Sec. 4.3) of a
+ * normalised FP64 vector v_dev (device, [dim]); occ: host [omega].  Synchronous.
+ */
+int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ);
+
+/* ------------------------------------------------ test hooks (device) ---- */
+
+/*
+ * Multi-dot with FP64 accumulation: out[j] = sum_i Q[j*ld + i] * p[i] for
+ * j < m (m <= 64), n elements.  dtype 0 = double, 1 = float storage.
+ * Q_dev, p_dev: device; out: host [m].  Synchronous.  (The reorthogonalisation
+ * projections of Sec. 3.4.)
+ */
+int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, int m,
+                      const void *p_dev, int64_t n, double *out);
+
+/*
+ * Lowest (and second-lowest) eigenvalue and the lowest eigenvector of the
+ * symmetric tridiagonal matrix with diagonal alpha[m] and off-diagonal
+ * beta[m-1] (the L matrix of Algorithm 2; QR_Decompose in App. B), computed
+ * by the device solver.  alpha, beta: host; theta: host [2]; s: host [m].
+ * m <= 64.  Synchronous.
+ */
+int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const double *beta,
+                            double *theta, double *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAIRDIAG_H */

@@ -1,0 +1,704 @@
+// pd_api.cu -- the C ABI (include/pairdiag.h): handle creation (block tables
+// of the basis), H*x entry points and the restarted-Lanczos driver.
+//
+// The driver follows Algorithm 2 of the paper with full reorthogonalisation
+// (classical Gram-Schmidt applied twice against every stored Lanczos vector),
+// the tridiagonal eigenproblem of each cycle solved on the device, and restart
+// from the ground Ritz vector (Sec. 3.4).  Convergence is the paper's
+// |beta_1/alpha_1| <= tol measured at the first step of each cycle (Sec. 5.1).
+#include "pd_internal.h"
+#include "../../include/pairdiag.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pd;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define PD_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define PD_TRY(call)                \
+    do {                            \
+        int s_ = (call);            \
+        if (s_ != PD_OK) return s_; \
+    } while (0)
+
+uint64_t host_binom(int n, int m)
+{
+    static uint64_t table[64][64];
+    static bool ready = false;
+    if (!ready) {
+        memset(table, 0, sizeof table);
+        for (int i = 0; i < 64; ++i) {
+            table[i][0] = 1;
+            for (int j = 1; j <= i; ++j) table[i][j] = table[i - 1][j - 1] + table[i - 1][j];
+        }
+        ready = true;
+    }
+    if (n < 0 || m < 0 || m > n || n > 63) return 0;
+    return table[n][m];
+}
+
+}  // namespace
+
+struct pairdiag {
+    int omega = 0, n = 0;
+    pairdiag_options opt{};
+    std::vector<double> e, G, d;
+    int64_t dim = 0, nnz = 0;
+    Blocks B{};
+    int device = 0;
+    cudaStream_t st = nullptr;
+    // tables
+    uint64_t *d_blk_h = nullptr, *d_blk_base = nullptr, *d_binom = nullptr;
+    uint16_t *d_lowword = nullptr, *d_rankL = nullptr;
+    double *d_G64 = nullptr, *d_d64 = nullptr;
+    float *d_G32 = nullptr, *d_d32 = nullptr;
+    int *d_counter = nullptr;
+    double *d_part = nullptr;        // partial sums of the streaming kernels
+    size_t part_count = 0;
+    LanczosScalars *d_S = nullptr;
+    double *d_small = nullptr;       // [8] small outputs
+    int hxgrid[2] = {0, 0};
+    int rgrid = 0;                   // grid of the per-row reductions
+    // Lanczos window (lazily allocated) per storage type
+    void *d_Q[2] = {nullptr, nullptr};
+    int Qwin[2] = {0, 0};
+    void *d_p[2] = {nullptr, nullptr};
+    double *d_v64 = nullptr, *d_w64 = nullptr;
+    std::vector<double> start;
+};
+
+namespace {
+
+void free_all(pairdiag *h)
+{
+    void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
+                    h->d_d64, h->d_G32, h->d_d32, h->d_counter, h->d_part, h->d_S, h->d_small,
+                    h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+int dalloc(T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA, "cudaMalloc(%zu bytes): %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
+    *p = static_cast<T *>(q);
+    return PD_OK;
+}
+
+template <typename T>
+int upload(T **p, const std::vector<T> &v)
+{
+    PD_TRY(dalloc(p, v.size()));
+    PD_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return PD_OK;
+}
+
+// words of `bits` bits with `c` set bits, ascending (Gosper's successor)
+void words_with_popcount(int bits, int c, std::vector<uint64_t> &out)
+{
+    if (c == 0) { out.push_back(0); return; }
+    if (c > bits) return;
+    uint64_t w = (c == 64) ? ~0ull : ((1ull << c) - 1ull);
+    const uint64_t last = w << (bits - c);
+    for (;;) {
+        out.push_back(w);
+        if (w == last) break;
+        const uint64_t lowest = w & (~w + 1ull);
+        const uint64_t ripple = w + lowest;
+        w = ripple | (((w ^ ripple) >> 2) / lowest);
+    }
+}
+
+uint64_t host_block_base(uint64_t hw, int L, int N)
+{
+    int ord = N - __builtin_popcountll(hw);
+    uint64_t s = 0;
+    for (int p = 0; p < 64; ++p)
+        if (hw >> p & 1ull) s += host_binom(L + p, ++ord);
+    return s;
+}
+
+int build_tables(pairdiag *h)
+{
+    const int omega = h->omega, N = h->n;
+    int L = h->opt.low_bits > 0 ? h->opt.low_bits : 12;
+    L = std::min(L, std::min(omega, kMaxLow));
+    const int H = omega - L;
+    // admissible k (pairs in the low orbits)
+    const int kmin = std::max(0, N - H), kmax = std::min(N, L);
+    int64_t nblocks = 0;
+    int max_block = 0, max_hh = 0;
+    for (int k = kmin; k <= kmax; ++k) {
+        nblocks += (int64_t)host_binom(H, N - k);
+        max_block = std::max(max_block, (int)host_binom(L, k));
+        max_hh = std::max(max_hh, (N - k) * (H - (N - k)));
+    }
+    if (nblocks > (int64_t)1 << 31) return fail(PD_ENOTSUP, "too many basis blocks (%lld)", (long long)nblocks);
+    std::vector<uint64_t> hw;
+    hw.reserve((size_t)nblocks);
+    for (int k = kmin; k <= kmax; ++k) words_with_popcount(H, N - k, hw);
+    std::sort(hw.begin(), hw.end());
+    std::vector<uint64_t> base(hw.size());
+    uint64_t run = 0;
+    for (size_t b = 0; b < hw.size(); ++b) {
+        base[b] = host_block_base(hw[b], L, N);
+        if (base[b] != run) return fail(PD_ECUDA, "internal: block index mismatch at block %zu", b);
+        run += host_binom(L, N - __builtin_popcountll(hw[b]));
+    }
+    if ((int64_t)run != h->dim) return fail(PD_ECUDA, "internal: blocks cover %llu of %lld states",
+                                            (unsigned long long)run, (long long)h->dim);
+    // low-word tables
+    const int nL = 1 << L;
+    std::vector<uint16_t> lowword(nL), rankL(nL);
+    std::vector<int> fill(L + 2, 0);
+    int off[kMaxLow + 2];
+    off[0] = 0;
+    for (int k = 0; k <= L; ++k) off[k + 1] = off[k] + (int)host_binom(L, k);
+    for (int w = 0; w < nL; ++w) {
+        const int k = __builtin_popcount(w);
+        rankL[w] = (uint16_t)fill[k];
+        lowword[off[k] + fill[k]] = (uint16_t)w;
+        ++fill[k];
+    }
+    std::vector<uint64_t> binom(64 * 64);
+    for (int i = 0; i < 64; ++i)
+        for (int j = 0; j < 64; ++j) binom[i * 64 + j] = host_binom(i, j);
+
+    PD_TRY(upload(&h->d_blk_h, hw));
+    PD_TRY(upload(&h->d_blk_base, base));
+    PD_TRY(upload(&h->d_lowword, lowword));
+    PD_TRY(upload(&h->d_rankL, rankL));
+    PD_TRY(upload(&h->d_binom, binom));
+
+    Blocks &B = h->B;
+    B.omega = omega; B.n = N; B.L = L; B.H = H;
+    B.nblocks = (int64_t)hw.size();
+    B.max_block = max_block;
+    B.max_hh = max_hh;
+    B.blk_h = h->d_blk_h; B.blk_base = h->d_blk_base;
+    B.lowword = h->d_lowword; B.rankL = h->d_rankL; B.binom = h->d_binom;
+    for (int k = 0; k <= kMaxLow + 1; ++k) B.lo_off[k] = (k <= L + 1) ? off[k] : off[L + 1];
+    return PD_OK;
+}
+
+int ensure_window(pairdiag *h, int dtype, int window)
+{
+    const size_t es = dtype == 0 ? sizeof(double) : sizeof(float);
+    if (h->d_Q[dtype] && h->Qwin[dtype] >= window) return PD_OK;
+    if (h->d_Q[dtype]) { cudaFree(h->d_Q[dtype]); h->d_Q[dtype] = nullptr; }
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, es * (size_t)window * (size_t)h->dim);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PD_ENOMEM, "Lanczos window of %d x %lld elements: %s", window, (long long)h->dim,
+                    cudaGetErrorString(e));
+    }
+    h->d_Q[dtype] = q;
+    h->Qwin[dtype] = window;
+    if (!h->d_p[dtype]) {
+        e = cudaMalloc(&h->d_p[dtype], es * (size_t)h->dim);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(PD_ENOMEM, "work vector: %s", cudaGetErrorString(e)); }
+    }
+    return PD_OK;
+}
+
+int ensure_fp64_pair(pairdiag *h)
+{
+    if (!h->d_v64) PD_TRY(dalloc(&h->d_v64, (size_t)h->dim));
+    if (!h->d_w64) PD_TRY(dalloc(&h->d_w64, (size_t)h->dim));
+    return PD_OK;
+}
+
+int hx(pairdiag *h, int precision, const void *x, void *y)
+{
+    HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
+    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_counter, h->hxgrid[precision], h->st));
+    return PD_OK;
+}
+
+template <typename T>
+T *vec(void *base, int64_t i, int64_t dim) { return static_cast<T *>(base) + i * dim; }
+
+void *qvec(pairdiag *h, int dtype, int i)
+{
+    const size_t es = dtype == 0 ? 8 : 4;
+    return static_cast<char *>(h->d_Q[dtype]) + es * (size_t)i * (size_t)h->dim;
+}
+
+struct CycleStats {
+    int iterations = 0;
+    int restarts = 0;
+    double rel = INFINITY;       // |beta_1/alpha_1| of the last restart vector
+    double energy = 0.0;         // Rayleigh quotient (converged) or last Ritz value
+    double gap = INFINITY;
+    bool converged = false;
+};
+
+// Restarted Lanczos on storage type dtype.  Q_0 holds the start vector (any
+// norm).  On return Q_0 is the normalised best vector.
+int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &cs)
+{
+    const int64_t dim = h->dim;
+    const int m = (int)std::min<int64_t>(std::max(1, h->opt.window), std::min<int64_t>(dim, kMaxWindow));
+    cudaStream_t st = h->st;
+    LanczosScalars *S = h->d_S;
+    void *Q = h->d_Q[dtype];
+    void *p = h->d_p[dtype];
+    // normalise the start vector
+    PD_CUDA(multidot_launch(dtype, Q, dim, 1, Q, dim, h->d_part, &S->dots[0], st));
+    PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
+    double host_ab[2];
+    for (int cycle = 0; cycle <= max_cycles; ++cycle) {
+        int used = 0;
+        double tnorm = 0.0;
+        for (int i = 0; i < m; ++i) {
+            PD_TRY(hx(h, dtype, qvec(h, dtype, i), p));
+            ++cs.iterations;
+            PD_CUDA(multidot_launch(dtype, Q, dim, i + 1, p, dim, h->d_part, S->c1, st));
+            PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c1, p, dim, h->d_part, nullptr, st));
+            PD_CUDA(multidot_launch(dtype, Q, dim, i + 1, p, dim, h->d_part, S->c2, st));
+            PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st));
+            PD_CUDA(finalize_step_launch(S, i, st));
+            PD_CUDA(cudaMemcpyAsync(&host_ab[0], &S->alpha[i], sizeof(double), cudaMemcpyDeviceToHost, st));
+            PD_CUDA(cudaMemcpyAsync(&host_ab[1], &S->beta[i], sizeof(double), cudaMemcpyDeviceToHost, st));
+            PD_CUDA(cudaStreamSynchronize(st));
+            used = i + 1;
+            const double a = host_ab[0], b = host_ab[1];
+            if (!std::isfinite(a) || !std::isfinite(b))
+                return fail(PD_ECUDA, "non-finite Lanczos coefficient at step %d", i);
+            if (i == 0) {
+                cs.rel = (b == 0.0) ? 0.0 : b / std::fabs(a);
+                cs.energy = a;
+                if (h->opt.mode == 0 && cs.rel <= tol) {
+                    cs.converged = true;
+                    return PD_OK;
+                }
+            }
+            tnorm = std::max(tnorm, std::fabs(a) + b);
+            if (i + 1 == m || b <= 1e-13 * tnorm) break;
+            PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i + 1), dim, &S->beta[i], 0, st));
+        }
+        PD_CUDA(tridiag_launch(S, used, st));
+        PD_CUDA(ritz_launch(dtype, Q, dim, used, S->s, dim, h->d_part, &S->norm2, st));
+        PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->norm2, 1, st));
+        double th[2];
+        PD_CUDA(cudaMemcpyAsync(th, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaStreamSynchronize(st));
+        cs.energy = th[0];
+        cs.gap = th[1] - th[0];
+        if (h->opt.mode == 1) {
+            cs.converged = true;
+            return PD_OK;
+        }
+        if (cycle < max_cycles) ++cs.restarts;
+    }
+    return PD_OK;
+}
+
+int init_start(pairdiag *h, int dtype)
+{
+    void *q0 = qvec(h, dtype, 0);
+    const int64_t dim = h->dim;
+    switch (h->opt.start) {
+    case PD_START_RANDOM:
+        PD_CUDA(random_start_launch(dtype, q0, dim, h->opt.seed, h->st));
+        break;
+    case PD_START_FIRST:
+    case PD_START_HF: {
+        int64_t pos = 0;
+        if (h->opt.start == PD_START_HF) {
+            double dmin, dmax;
+            PD_TRY(pairdiag_monopole(h, &dmin, &dmax, &pos));
+        }
+        const size_t es = dtype == 0 ? 8 : 4;
+        PD_CUDA(cudaMemsetAsync(q0, 0, es * (size_t)dim, h->st));
+        const double one = 1.0;
+        const float onef = 1.0f;
+        PD_CUDA(cudaMemcpyAsync(static_cast<char *>(q0) + es * (size_t)pos, dtype == 0 ? (const void *)&one : (const void *)&onef,
+                                es, cudaMemcpyHostToDevice, h->st));
+        PD_CUDA(cudaStreamSynchronize(h->st));
+        break;
+    }
+    case PD_START_USER: {
+        if ((int64_t)h->start.size() != dim) return fail(PD_EINVAL, "no start vector set (pairdiag_set_start)");
+        PD_TRY(ensure_fp64_pair(h));
+        PD_CUDA(cudaMemcpyAsync(h->d_v64, h->start.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, h->st));
+        PD_CUDA(convert_launch(dtype, q0, 0, h->d_v64, dim, h->st));
+        break;
+    }
+    default:
+        return fail(PD_EINVAL, "unknown start kind %d", h->opt.start);
+    }
+    return PD_OK;
+}
+
+// FP64 Rayleigh quotient and residual of Q_0 (of storage dtype): v64 <- Q_0,
+// w64 <- H v64.  Returns lambda, relative residual ||Hv - lambda v|| / |lambda| / ||v||.
+int rayleigh64(pairdiag *h, int dtype, double *lambda, double *rel)
+{
+    const int64_t dim = h->dim;
+    PD_TRY(ensure_fp64_pair(h));
+    PD_CUDA(convert_launch(0, h->d_v64, dtype, qvec(h, dtype, 0), dim, h->st));
+    PD_TRY(hx(h, 0, h->d_v64, h->d_w64));
+    LanczosScalars *S = h->d_S;
+    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_w64, dim, h->d_part, &S->dots[0], h->st));
+    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &S->dots[1], h->st));
+    double vv_vw[2];
+    PD_CUDA(cudaMemcpyAsync(vv_vw, &S->dots[0], 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    const double lam = vv_vw[0] / vv_vw[1];
+    PD_CUDA(cudaMemcpyAsync(&S->dots[2], &lam, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    PD_CUDA(residual_launch(h->d_w64, h->d_v64, &S->dots[2], nullptr, dim, h->d_part, &S->dots[3], h->st));
+    double r2;
+    PD_CUDA(cudaMemcpyAsync(&r2, &S->dots[3], sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    *lambda = lam;
+    *rel = (r2 == 0.0) ? 0.0 : std::sqrt(r2 / vv_vw[1]) / std::fabs(lam);
+    return PD_OK;
+}
+
+int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool vec_is_host,
+                      double *vec_host, pairdiag_info *info)
+{
+    if (!h || !e0) return fail(PD_EINVAL, "null argument");
+    if (!(tol >= 0.0)) return fail(PD_EINVAL, "tol must be >= 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    PD_CUDA(cudaSetDevice(h->device));
+    const int64_t dim = h->dim;
+    const int win = std::min<int64_t>(std::max(1, h->opt.window), std::min<int64_t>(dim, kMaxWindow));
+    CycleStats cs;
+    int status = PD_OK;
+    int fp32_iters = 0;
+    int final_dtype = 0;
+    double energy = 0.0, rel = INFINITY;
+    if (h->opt.precision == PD_PREC_MIXED) {
+        PD_TRY(ensure_window(h, 1, win));
+        PD_TRY(init_start(h, 1));
+        const double tol32 = std::max(tol, h->opt.mixed_floor);
+        PD_TRY(run_cycles(h, 1, tol32, h->opt.max_restarts, cs));
+        fp32_iters = cs.iterations;
+        double lam, r;
+        PD_TRY(rayleigh64(h, 1, &lam, &r));
+        energy = lam; rel = r;
+        if (r <= tol || h->opt.mode == 1) {
+            cs.converged = true;
+            final_dtype = -1;                  // vector lives in d_v64
+        } else {
+            // continue in FP64 from the refined vector
+            PD_TRY(ensure_window(h, 0, win));
+            PD_CUDA(cudaMemcpyAsync(qvec(h, 0, 0), h->d_v64, sizeof(double) * dim, cudaMemcpyDeviceToDevice, h->st));
+            CycleStats c64;
+            const int left = std::max(0, h->opt.max_restarts - cs.restarts);
+            PD_TRY(run_cycles(h, 0, tol, left, c64));
+            cs.iterations += c64.iterations;
+            cs.restarts += c64.restarts;
+            cs.converged = c64.converged;
+            cs.gap = c64.gap;
+            energy = c64.energy;
+            rel = c64.rel;
+            final_dtype = 0;
+        }
+    } else {
+        PD_TRY(ensure_window(h, 0, win));
+        PD_TRY(init_start(h, 0));
+        PD_TRY(run_cycles(h, 0, tol, h->opt.max_restarts, cs));
+        energy = cs.energy;
+        rel = cs.rel;
+        final_dtype = 0;
+        if (h->opt.mode == 1) {                // report the residual of the Ritz vector
+            double lam, r;
+            PD_TRY(rayleigh64(h, 0, &lam, &r));
+            rel = r;
+        }
+    }
+    if (!cs.converged) status = fail(PD_ENOCONV, "tolerance %.3g not reached after %d restarts (residual %.3g)",
+                                     tol, cs.restarts, rel);
+    // output vector
+    const double *src = final_dtype == -1 ? h->d_v64 : static_cast<const double *>(qvec(h, 0, 0));
+    if (final_dtype == -1) {                   // normalise the refined FP64 copy
+        PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &h->d_S->dots[0], h->st));
+        PD_CUDA(scale_launch(0, h->d_v64, h->d_v64, dim, &h->d_S->dots[0], 1, h->st));
+    }
+    if (vec_dev) PD_CUDA(cudaMemcpyAsync(vec_dev, src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, h->st));
+    if (vec_is_host && vec_host)
+        PD_CUDA(cudaMemcpyAsync(vec_host, src, sizeof(double) * dim, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    *e0 = energy;
+    if (info) {
+        info->dim = dim;
+        info->nnz_offdiag = h->nnz;
+        info->iterations = cs.iterations;
+        info->iterations_fp32 = fp32_iters;
+        info->restarts = cs.restarts;
+        info->converged = cs.converged ? 1 : 0;
+        info->rel_residual = rel;
+        info->gap_estimate = cs.gap;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pairdiag_default_options(pairdiag_options *opt)
+{
+    if (!opt) return;
+    opt->window = 20;
+    opt->max_restarts = 500;
+    opt->precision = PD_PREC_FP64;
+    opt->start = PD_START_RANDOM;
+    opt->seed = 1;
+    opt->mode = 0;
+    opt->low_bits = 0;
+    opt->mixed_floor = 5e-6;
+}
+
+const char *pairdiag_strerror(int code)
+{
+    switch (code) {
+    case PD_OK: return "success";
+    case PD_EINVAL: return "invalid argument";
+    case PD_ENOMEM: return "out of device memory";
+    case PD_ENOCONV: return "Lanczos did not converge";
+    case PD_ETIMEOUT: return "device wait timed out";
+    case PD_ECUDA: return "CUDA error";
+    case PD_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+const char *pairdiag_last_error(void) { return g_last_error.c_str(); }
+
+int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
+                    const pairdiag_options *opt, pairdiag_t **out)
+{
+    if (!out) return fail(PD_EINVAL, "out is null");
+    *out = nullptr;
+    if (omega < 1 || omega > kMaxOmega) return fail(PD_EINVAL, "omega=%d outside 1..%d", omega, kMaxOmega);
+    if (n_pairs < 0 || n_pairs > omega) return fail(PD_EINVAL, "n_pairs=%d outside 0..omega", n_pairs);
+    if (!e || !G) return fail(PD_EINVAL, "e or G is null");
+    for (int i = 0; i < omega; ++i)
+        if (!std::isfinite(e[i])) return fail(PD_EINVAL, "e[%d] is not finite", i);
+    for (int i = 0; i < omega; ++i)
+        for (int j = 0; j < omega; ++j) {
+            if (!std::isfinite(G[i * omega + j])) return fail(PD_EINVAL, "G[%d][%d] is not finite", i, j);
+            if (G[i * omega + j] != G[j * omega + i]) return fail(PD_EINVAL, "G is not symmetric at (%d,%d)", i, j);
+        }
+    pairdiag_options o;
+    pairdiag_default_options(&o);
+    if (opt) o = *opt;
+    if (o.window < 1 || o.window > kMaxWindow) return fail(PD_EINVAL, "window=%d outside 1..%d", o.window, kMaxWindow);
+    if (o.precision != PD_PREC_FP64 && o.precision != PD_PREC_MIXED) return fail(PD_EINVAL, "bad precision");
+    if (o.mode != 0 && o.mode != 1) return fail(PD_EINVAL, "bad mode");
+    if (o.low_bits < 0 || o.low_bits > kMaxLow) return fail(PD_EINVAL, "low_bits outside 0..%d", kMaxLow);
+    if (o.max_restarts < 0) return fail(PD_EINVAL, "max_restarts < 0");
+
+    pairdiag *h = new pairdiag();
+    h->omega = omega; h->n = n_pairs; h->opt = o;
+    h->e.assign(e, e + omega);
+    h->G.assign(G, G + (size_t)omega * omega);
+    h->d.resize(omega);
+    for (int p = 0; p < omega; ++p) h->d[p] = 2.0 * e[p] + G[p * omega + p];
+    h->dim = (int64_t)host_binom(omega, n_pairs);
+    h->nnz = h->dim * (int64_t)n_pairs * (int64_t)(omega - n_pairs);
+    int st = PD_OK;
+    do {
+        if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); st = fail(PD_ECUDA, "no CUDA device"); break; }
+        if ((st = build_tables(h)) != PD_OK) break;
+        std::vector<float> G32(h->G.begin(), h->G.end()), d32(h->d.begin(), h->d.end());
+        if ((st = upload(&h->d_G64, h->G)) != PD_OK) break;
+        if ((st = upload(&h->d_d64, h->d)) != PD_OK) break;
+        if ((st = upload(&h->d_G32, G32)) != PD_OK) break;
+        if ((st = upload(&h->d_d32, d32)) != PD_OK) break;
+        if ((st = dalloc(&h->d_counter, 4)) != PD_OK) break;
+        h->hxgrid[0] = hx_grid(h->B, 0);
+        h->hxgrid[1] = hx_grid(h->B, 1);
+        h->rgrid = (int)std::min<int64_t>(h->B.nblocks, 152 * 4);
+        h->part_count = (size_t)std::max(vec_grid(), h->rgrid) * kMaxWindow;
+        if ((st = dalloc(&h->d_part, h->part_count)) != PD_OK) break;
+        if ((st = dalloc(&h->d_S, 1)) != PD_OK) break;
+        if ((st = dalloc(&h->d_small, 8)) != PD_OK) break;
+        if (cudaMemset(h->d_S, 0, sizeof(LanczosScalars)) != cudaSuccess) { st = fail(PD_ECUDA, "memset"); break; }
+    } while (0);
+    if (st != PD_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PD_OK;
+}
+
+void pairdiag_destroy(pairdiag_t *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+int pairdiag_set_stream(pairdiag_t *h, void *stream)
+{
+    if (!h) return fail(PD_EINVAL, "null handle");
+    h->st = static_cast<cudaStream_t>(stream);
+    return PD_OK;
+}
+
+int64_t pairdiag_dim(const pairdiag_t *h) { return h ? h->dim : -1; }
+int64_t pairdiag_nnz(const pairdiag_t *h) { return h ? h->nnz : -1; }
+
+int pairdiag_basis_dev(const pairdiag_t *h, int64_t first, int64_t count, uint64_t *out_dev)
+{
+    if (!h || (!out_dev && count > 0)) return fail(PD_EINVAL, "null argument");
+    if (first < 0 || count < 0 || first + count > h->dim) return fail(PD_EINVAL, "range outside [0, dim)");
+    PD_CUDA(basis_launch(h->omega, h->n, h->d_binom, first, count, out_dev, h->st));
+    return PD_OK;
+}
+
+int pairdiag_basis(const pairdiag_t *h, uint64_t *out)
+{
+    if (!h || !out) return fail(PD_EINVAL, "null argument");
+    uint64_t *d = nullptr;
+    PD_TRY(dalloc(&d, (size_t)h->dim));
+    int st = pairdiag_basis_dev(h, 0, h->dim, d);
+    if (st == PD_OK) {
+        cudaError_t e1 = cudaMemcpyAsync(out, d, sizeof(uint64_t) * h->dim, cudaMemcpyDeviceToHost, h->st);
+        cudaError_t e2 = cudaStreamSynchronize(h->st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) st = fail(PD_ECUDA, "basis copy failed");
+    }
+    cudaFree(d);
+    return st;
+}
+
+int pairdiag_rank_dev(const pairdiag_t *h, const uint64_t *states_dev, int64_t count, uint64_t *ranks_dev)
+{
+    if (!h || ((!states_dev || !ranks_dev) && count > 0) || count < 0) return fail(PD_EINVAL, "bad argument");
+    PD_CUDA(rank_launch(h->omega, h->n, h->d_binom, states_dev, count, ranks_dev, h->st));
+    return PD_OK;
+}
+
+int pairdiag_hx_dev(pairdiag_t *h, int precision, const void *x_dev, void *y_dev)
+{
+    if (!h || !x_dev || !y_dev) return fail(PD_EINVAL, "null argument");
+    if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED) return fail(PD_EINVAL, "bad precision");
+    if (x_dev == y_dev) return fail(PD_EINVAL, "x and y must not overlap");
+    return hx(h, precision, x_dev, y_dev);
+}
+
+int pairdiag_hx(pairdiag_t *h, const double *x, double *y)
+{
+    if (!h || !x || !y) return fail(PD_EINVAL, "null argument");
+    PD_TRY(ensure_fp64_pair(h));
+    PD_CUDA(cudaMemcpyAsync(h->d_v64, x, sizeof(double) * h->dim, cudaMemcpyHostToDevice, h->st));
+    PD_TRY(hx(h, 0, h->d_v64, h->d_w64));
+    PD_CUDA(cudaMemcpyAsync(y, h->d_w64, sizeof(double) * h->dim, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+int pairdiag_monopole(pairdiag_t *h, double *dmin, double *dmax, int64_t *pos_min)
+{
+    if (!h || !dmin || !dmax || !pos_min) return fail(PD_EINVAL, "null argument");
+    PD_CUDA(monopole_launch(h->B, h->d_d64, h->d_part, h->rgrid, h->d_small, h->st));
+    double out[3];
+    PD_CUDA(cudaMemcpyAsync(out, h->d_small, sizeof out, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    *dmin = out[0];
+    *dmax = out[1];
+    int64_t pos;
+    memcpy(&pos, &out[2], sizeof pos);
+    *pos_min = pos;
+    return PD_OK;
+}
+
+int pairdiag_set_start(pairdiag_t *h, const double *v)
+{
+    if (!h || !v) return fail(PD_EINVAL, "null argument");
+    h->start.assign(v, v + h->dim);
+    return PD_OK;
+}
+
+int pairdiag_ground_state(pairdiag_t *h, double tol, double *e0, double *vec, pairdiag_info *info)
+{
+    return ground_state_impl(h, tol, e0, nullptr, true, vec, info);
+}
+
+int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec_dev, pairdiag_info *info)
+{
+    return ground_state_impl(h, tol, e0, vec_dev, false, nullptr, info);
+}
+
+int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ)
+{
+    if (!h || !v_dev || !occ) return fail(PD_EINVAL, "null argument");
+    PD_CUDA(occupations_launch(h->B, v_dev, h->d_part, h->rgrid, h->d_S->s, h->st));
+    PD_CUDA(cudaMemcpyAsync(occ, h->d_S->s, sizeof(double) * h->omega, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, int m, const void *p_dev,
+                      int64_t n, double *out)
+{
+    if (!h || !Q_dev || !p_dev || !out) return fail(PD_EINVAL, "null argument");
+    if (m < 1 || m > kMaxWindow || n < 0 || (dtype != 0 && dtype != 1)) return fail(PD_EINVAL, "bad sizes");
+    PD_CUDA(multidot_launch(dtype, Q_dev, ld, m, p_dev, n, h->d_part, h->d_S->c1, h->st));
+    PD_CUDA(cudaMemcpyAsync(out, h->d_S->c1, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const double *beta, double *theta,
+                            double *s)
+{
+    if (!h || !alpha || !theta || !s || (m > 1 && !beta)) return fail(PD_EINVAL, "null argument");
+    if (m < 1 || m > kMaxWindow) return fail(PD_EINVAL, "m outside 1..%d", kMaxWindow);
+    LanczosScalars *S = h->d_S;
+    PD_CUDA(cudaMemcpyAsync(S->alpha, alpha, sizeof(double) * m, cudaMemcpyHostToDevice, h->st));
+    if (m > 1) PD_CUDA(cudaMemcpyAsync(S->beta, beta, sizeof(double) * (m - 1), cudaMemcpyHostToDevice, h->st));
+    PD_CUDA(tridiag_launch(S, m, h->st));
+    PD_CUDA(cudaMemcpyAsync(theta, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaMemcpyAsync(s, S->s, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,426 @@
+// pd_hx.cu -- on-the-fly H*x in the seniority-zero pair basis (Sec. 3.3 and
+// Eq. "diagonal" of the paper), plus the per-row reductions that share its
+// block structure (Monopole_Min/Max, occupation numbers).
+//
+// y_s = (sum_{p in s} d_p) x_s + sum_{o in s, e not in s} G_eo x_{t(s,o,e)},
+// d_p = 2 e_p + G_pp, t = s with the pair moved from orbit o to orbit e.
+//
+// One CTA owns one basis block at a time (all states sharing a high word h,
+// see pd_internal.h); blocks are handed out through an atomic counter so that
+// blocks of different sizes balance across the persistent grid.  For the
+// block's rows (low words l, one or more per thread) the N(Omega-N) hops fall
+// into four classes:
+//   low->low   : target in the same block; x block staged in shared memory,
+//                target offset from the shared rank table of L-bit words;
+//   high->high : target block h^o^e has the SAME row offsets, so the gather is
+//                a contiguous, coalesced read of that block with one
+//                CTA-uniform coefficient G_eo;
+//   high->low  : target block h - o (k+1 low pairs) staged in shared memory
+//                once and reused by all rows and all empty low orbits;
+//   low->high  : target block h + e (k-1 low pairs), likewise.
+// No tensor cores: this is a sparse gather, not a dense contraction.
+#include "pd_internal.h"
+
+#include <cstdio>
+
+namespace pd {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename A>
+struct HHop {            // one high->high hop of the current block
+    uint64_t base;       // first index of the target block
+    A g;                 // G_eo
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+struct Layout {
+    size_t G, d, rank, x, xn, hh, mx, total;
+};
+
+template <typename T, typename A>
+__host__ __device__ inline Layout layout(int omega, int L, int H, int max_block, int max_hh)
+{
+    Layout s;
+    size_t off = 0;
+    s.G = off;    off = align16(off + sizeof(A) * omega * omega);
+    s.d = off;    off = align16(off + sizeof(A) * omega);
+    s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
+    s.x = off;    off = align16(off + sizeof(T) * max_block);
+    s.xn = off;   off = align16(off + sizeof(T) * max_block);
+    s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
+    s.mx = off;   off = align16(off + sizeof(uint64_t) * (H > 0 ? H : 1));
+    s.total = off;
+    return s;
+}
+
+// position of the n-th (0-based) set bit of w
+__device__ __forceinline__ int nth_set_bit(uint64_t w, int n)
+{
+    for (int i = 0; i < n; ++i) w &= w - 1;
+    return __ffsll((long long)w) - 1;
+}
+
+// index of the first state of the block with high word h (Sec. 3.2 hash,
+// restricted to the high bits: ordinals k+1..N at positions L+p)
+__device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
+                                               const uint64_t *__restrict__ binom)
+{
+    int ord = N - __popcll(h);
+    uint64_t s = 0;
+    while (h) {
+        const int p = __ffsll((long long)h) - 1;
+        h &= h - 1;
+        ++ord;
+        s += __ldg(binom + (L + p) * kBinomStride + ord);
+    }
+    return s;
+}
+
+template <typename T, typename A, int R>
+__global__ void __launch_bounds__(kThreads)
+hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
+          const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_next;
+    const int omega = B.omega, L = B.L, H = B.H, N = B.n;
+    const Layout lay = layout<T, A>(omega, L, H, B.max_block, B.max_hh);
+    A *sG = reinterpret_cast<A *>(smem + lay.G);
+    A *sd = reinterpret_cast<A *>(smem + lay.d);
+    uint16_t *sRank = reinterpret_cast<uint16_t *>(smem + lay.rank);
+    T *sx = reinterpret_cast<T *>(smem + lay.x);
+    T *sxn = reinterpret_cast<T *>(smem + lay.xn);
+    HHop<A> *sHH = reinterpret_cast<HHop<A> *>(smem + lay.hh);
+    uint64_t *sMX = reinterpret_cast<uint64_t *>(smem + lay.mx);
+    const int tid = threadIdx.x;
+
+    for (int i = tid; i < omega * omega; i += kThreads) sG[i] = Gg[i];
+    for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
+    for (int i = tid; i < (1 << L); i += kThreads) sRank[i] = B.rankL[i];
+    const uint32_t maskL = (1u << L) - 1u;
+    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
+
+    for (;;) {
+        __syncthreads();                          // smem of the previous block is free
+        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long b = s_next;
+        if (b >= B.nblocks) break;
+
+        const uint64_t h = __ldg(B.blk_h + b);
+        const uint64_t base = __ldg(B.blk_base + b);
+        const int ph = __popcll(h);
+        const int k = N - ph;                     // pairs in the low orbits
+        const int nk = (int)__ldg(B.binom + L * kBinomStride + k);
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        const int nemp = H - ph;
+        const int nhh = ph * nemp;
+
+        // CTA-uniform hop tables of this block
+        for (int t = tid; t < nhh; t += kThreads) {
+            const int a = t / nemp, c = t - a * nemp;
+            const int o = nth_set_bit(h, a);
+            const int q = nth_set_bit(~h & maskH, c);
+            sHH[t].base = block_base(h ^ (1ull << o) ^ (1ull << q), L, N, B.binom);
+            sHH[t].g = sG[(L + q) * omega + (L + o)];
+        }
+        for (int t = tid; t < H; t += kThreads) {
+            const uint64_t bit = 1ull << t;
+            const bool occ = (h & bit) != 0;
+            const bool ok = occ ? (k + 1 <= L) : (k >= 1);
+            sMX[t] = ok ? block_base(h ^ bit, L, N, B.binom) : ~0ull;
+        }
+        for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
+        __syncthreads();
+
+        A Dh = A(0);
+        for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
+
+        uint32_t lr[R];
+        A acc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            lr[i] = 0;
+            acc[i] = A(0);
+            if (r < nk) {
+                const uint32_t l = lw[r];
+                lr[i] = l;
+                A D = A(0);
+                for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
+                acc[i] = (D + Dh) * A(sx[r]);
+            }
+        }
+
+        // low -> low
+        if (k > 0 && k < L) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (tid + i * kThreads < nk) {
+                    const uint32_t l = lr[i];
+                    A a = acc[i];
+                    uint32_t occ = l;
+                    for (int u = 0; u < k; ++u) {
+                        const int o = __ffs(occ) - 1;
+                        occ &= occ - 1;
+                        const uint32_t lo = l ^ (1u << o);
+                        uint32_t emp = ~l & maskL;
+                        for (int v = 0; v < L - k; ++v) {
+                            const int q = __ffs(emp) - 1;
+                            emp &= emp - 1;
+                            a += sG[q * omega + o] * A(sx[sRank[lo | (1u << q)]]);
+                        }
+                    }
+                    acc[i] = a;
+                }
+            }
+        }
+
+        // high -> high: same offsets in the target block
+        for (int j = 0; j < nhh; ++j) {
+            const T *xb = x + sHH[j].base;
+            const A g = sHH[j].g;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = tid + i * kThreads;
+                if (r < nk) acc[i] += g * A(__ldg(xb + r));
+            }
+        }
+
+        // high <-> low: stage each neighbouring block once
+        for (int t = 0; t < H; ++t) {
+            const uint64_t b2 = sMX[t];
+            if (b2 == ~0ull) continue;            // CTA-uniform
+            const bool occ_t = (h >> t) & 1ull;
+            const int n2 = (int)__ldg(B.binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
+            __syncthreads();
+            for (int r = tid; r < n2; r += kThreads) sxn[r] = x[b2 + r];
+            __syncthreads();
+            const int go = L + t;
+            if (occ_t) {                           // pair: high orbit go -> empty low orbit q
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (tid + i * kThreads < nk) {
+                        const uint32_t l = lr[i];
+                        A a = acc[i];
+                        uint32_t emp = ~l & maskL;
+                        for (int v = 0; v < L - k; ++v) {
+                            const int q = __ffs(emp) - 1;
+                            emp &= emp - 1;
+                            a += sG[q * omega + go] * A(sxn[sRank[l | (1u << q)]]);
+                        }
+                        acc[i] = a;
+                    }
+                }
+            } else {                               // pair: occupied low orbit o -> high orbit go
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (tid + i * kThreads < nk) {
+                        const uint32_t l = lr[i];
+                        A a = acc[i];
+                        uint32_t occ = l;
+                        for (int u = 0; u < k; ++u) {
+                            const int o = __ffs(occ) - 1;
+                            occ &= occ - 1;
+                            a += sG[go * omega + o] * A(sxn[sRank[l ^ (1u << o)]]);
+                        }
+                        acc[i] = a;
+                    }
+                }
+            }
+        }
+
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) y[base + r] = T(acc[i]);
+        }
+    }
+}
+
+template <typename T, typename A, int R>
+cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, void *y,
+                     unsigned long long *counter, int grid, cudaStream_t st)
+{
+    const size_t smem = layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+    cudaError_t err = cudaFuncSetAttribute(hx_kernel<T, A, R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return err;
+    hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                     static_cast<T *>(y), counter);
+    return cudaGetLastError();
+}
+
+template <typename T, typename A>
+cudaError_t launch_prec(const Blocks &B, const A *G, const A *d, const void *x, void *y,
+                        unsigned long long *counter, int grid, cudaStream_t st)
+{
+    const int rows = (B.max_block + kThreads - 1) / kThreads;
+    if (rows <= 1) return launch_t<T, A, 1>(B, G, d, x, y, counter, grid, st);
+    if (rows <= 2) return launch_t<T, A, 2>(B, G, d, x, y, counter, grid, st);
+    if (rows <= 4) return launch_t<T, A, 4>(B, G, d, x, y, counter, grid, st);
+    return launch_t<T, A, 8>(B, G, d, x, y, counter, grid, st);
+}
+
+template <typename T, typename A>
+int grid_prec(const Blocks &B)
+{
+    const size_t smem = layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+    const int rows = (B.max_block + kThreads - 1) / kThreads;
+    const void *fn = rows <= 1 ? (const void *)hx_kernel<T, A, 1>
+                   : rows <= 2 ? (const void *)hx_kernel<T, A, 2>
+                   : rows <= 4 ? (const void *)hx_kernel<T, A, 4>
+                               : (const void *)hx_kernel<T, A, 8>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > B.nblocks) g = B.nblocks;
+    return (int)(g > 0 ? g : 1);
+}
+
+// ---- Monopole_Min / Monopole_Max / Posit_Min ---------------------------------
+// Diagonal of each row summed over its occupied orbits in ascending orbit
+// order (the oracle's order, so the values agree bit for bit).
+__global__ void __launch_bounds__(kThreads)
+monopole_kernel(const Blocks B, const double *__restrict__ d, double *__restrict__ part)
+{
+    double vmin = INFINITY, vmax = -INFINITY;
+    long long imin = LLONG_MAX;
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            double D = 0.0;
+            for (uint32_t w = lw[r]; w; w &= w - 1) D += d[__ffs(w) - 1];
+            for (uint64_t w = h; w; w &= w - 1) D += d[B.L + __ffsll((long long)w) - 1];
+            const long long idx = (long long)(base + r);
+            if (D < vmin || (D == vmin && idx < imin)) { vmin = D; imin = idx; }
+            if (D > vmax) vmax = D;
+        }
+    }
+    __shared__ double smin[kThreads], smax[kThreads];
+    __shared__ long long sidx[kThreads];
+    smin[threadIdx.x] = vmin; smax[threadIdx.x] = vmax; sidx[threadIdx.x] = imin;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const int o = threadIdx.x + s;
+            if (smin[o] < smin[threadIdx.x] || (smin[o] == smin[threadIdx.x] && sidx[o] < sidx[threadIdx.x])) {
+                smin[threadIdx.x] = smin[o]; sidx[threadIdx.x] = sidx[o];
+            }
+            if (smax[o] > smax[threadIdx.x]) smax[threadIdx.x] = smax[o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = smin[0];
+        part[3 * blockIdx.x + 1] = smax[0];
+        part[3 * blockIdx.x + 2] = __longlong_as_double(sidx[0]);
+    }
+}
+
+__global__ void monopole_final(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double vmin = INFINITY, vmax = -INFINITY;
+    long long imin = LLONG_MAX;
+    for (int i = 0; i < n; ++i) {
+        const double a = part[3 * i], c = part[3 * i + 1];
+        const long long j = __double_as_longlong(part[3 * i + 2]);
+        if (a < vmin || (a == vmin && j < imin)) { vmin = a; imin = j; }
+        if (c > vmax) vmax = c;
+    }
+    out[0] = vmin; out[1] = vmax; out[2] = __longlong_as_double(imin);
+}
+
+// ---- occupation numbers 2 <v| S+_p S-_p |v> ------------------------------------
+__global__ void __launch_bounds__(kThreads)
+occ_kernel(const Blocks B, const double *__restrict__ v, double *__restrict__ part)
+{
+    __shared__ double acc[kMaxOmega];
+    __shared__ double blk_sum[kThreads];
+    for (int p = threadIdx.x; p < B.omega; p += blockDim.x) acc[p] = 0.0;
+    __syncthreads();
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        double mine = 0.0;
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            const double w = v[base + r] * v[base + r];
+            mine += w;
+            for (uint32_t m = lw[r]; m; m &= m - 1) atomicAdd(&acc[__ffs(m) - 1], w);
+        }
+        blk_sum[threadIdx.x] = mine;
+        __syncthreads();
+        for (int s = kThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) blk_sum[threadIdx.x] += blk_sum[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            for (uint64_t m = h; m; m &= m - 1) acc[B.L + __ffsll((long long)m) - 1] += blk_sum[0];
+        __syncthreads();
+    }
+    for (int p = threadIdx.x; p < B.omega; p += blockDim.x) part[blockIdx.x * B.omega + p] = acc[p];
+}
+
+__global__ void occ_final(const double *__restrict__ part, int n, int omega, double *__restrict__ out)
+{
+    const int p = threadIdx.x;
+    if (p >= omega) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i * omega + p];
+    out[p] = 2.0 * s;
+}
+
+}  // namespace
+
+size_t hx_smem_bytes(const Blocks &B, int precision)
+{
+    return precision == 0 ? layout<double, double>(B.omega, B.L, B.H, B.max_block, B.max_hh).total
+                          : layout<float, float>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+}
+
+int hx_grid(const Blocks &B, int precision)
+{
+    return precision == 0 ? grid_prec<double, double>(B) : grid_prec<float, float>(B);
+}
+
+cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
+                      int *counter, int grid, cudaStream_t st)
+{
+    auto *ctr = reinterpret_cast<unsigned long long *>(counter);
+    if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, ctr, grid, st);
+    return launch_prec<float, float>(B, P.G32, P.d32, x, y, ctr, grid, st);
+}
+
+cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,
+                            double *out, cudaStream_t st)
+{
+    monopole_kernel<<<grid, kThreads, 0, st>>>(B, d64, partials);
+    monopole_final<<<1, 32, 0, st>>>(partials, grid, out);
+    return cudaGetLastError();
+}
+
+cudaError_t occupations_launch(const Blocks &B, const double *v, double *partials, int grid,
+                               double *out, cudaStream_t st)
+{
+    occ_kernel<<<grid, kThreads, 0, st>>>(B, v, partials);
+    occ_final<<<1, 64, 0, st>>>(partials, grid, B.omega, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libpairdiag (include/pairdiag.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (PyTorch supplies device memory
+and streams); host buffers are numpy arrays.  If the library is missing, the
+import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+PD_OK, PD_EINVAL, PD_ENOMEM, PD_ENOCONV, PD_ETIMEOUT, PD_ECUDA, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+PD_PREC_FP64, PD_PREC_MIXED = 0, 1
+PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER = 0, 1, 2, 3
+
+
+class pairdiag_options(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("max_restarts", ctypes.c_int), ("precision", ctypes.c_int),
+                ("start", ctypes.c_int), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
+                ("low_bits", ctypes.c_int), ("mixed_floor", ctypes.c_double)]
+
+
+class pairdiag_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int64), ("nnz_offdiag", ctypes.c_int64), ("iterations", ctypes.c_int),
+                ("iterations_fp32", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("gap_estimate", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PairDiagError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+_lib = None
+
+_SIGNATURES = {
+    "pairdiag_default_options": (None, [ctypes.POINTER(pairdiag_options)]),
+    "pairdiag_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pairdiag_last_error": (ctypes.c_char_p, []),
+    "pairdiag_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(pairdiag_options),
+                                       ctypes.POINTER(_H)]),
+    "pairdiag_destroy": (None, [_H]),
+    "pairdiag_set_stream": (ctypes.c_int, [_H, _P]),
+    "pairdiag_dim": (ctypes.c_int64, [_H]),
+    "pairdiag_nnz": (ctypes.c_int64, [_H]),
+    "pairdiag_basis_dev": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _P]),
+    "pairdiag_basis": (ctypes.c_int, [_H, _P]),
+    "pairdiag_rank_dev": (ctypes.c_int, [_H, _P, ctypes.c_int64, _P]),
+    "pairdiag_hx_dev": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
+    "pairdiag_hx": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_monopole": (ctypes.c_int, [_H, _P, _P, _P]),
+    "pairdiag_set_start": (ctypes.c_int, [_H, _P]),
+    "pairdiag_ground_state": (ctypes.c_int, [_H, ctypes.c_double, _P, _P, ctypes.POINTER(pairdiag_info)]),
+    "pairdiag_ground_state_dev": (ctypes.c_int, [_H, ctypes.c_double, _P, _P, ctypes.POINTER(pairdiag_info)]),
+    "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
+    "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
+}
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib():
+    """Load libpairdiag.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not path.exists():
+            raise ImportError(f"libpairdiag.so not built at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(str(path))
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(code: int, allow=(PD_OK,)) -> int:
+    if code not in allow:
+        raise PairDiagError(code, lib().pairdiag_last_error().decode())
+    return code
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t, dtype=None):
+    """data_ptr() of a contiguous CUDA tensor (marshalling check only)."""
+    if not getattr(t, "is_cuda", False):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ ABI ----
+def pairdiag_default_options(**overrides) -> pairdiag_options:
+    o = pairdiag_options()
+    lib().pairdiag_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pairdiag_strerror(code: int) -> str:
+    return lib().pairdiag_strerror(code).decode()
+
+
+def pairdiag_create(omega: int, n_pairs: int, e, G, opt: pairdiag_options | None = None):
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    if e.shape != (omega,) or G.shape != (omega, omega):
+        raise ValueError("e must be [omega] and G [omega, omega]")
+    h = _H()
+    _check(lib().pairdiag_create(omega, n_pairs, _np_ptr(e), _np_ptr(G),
+                                 ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+    return h
+
+
+def pairdiag_destroy(h) -> None:
+    lib().pairdiag_destroy(h)
+
+
+def pairdiag_set_stream(h, stream) -> None:
+    ptr = getattr(stream, "cuda_stream", stream)
+    _check(lib().pairdiag_set_stream(h, ctypes.c_void_p(int(ptr))))
+
+
+def pairdiag_dim(h) -> int:
+    return int(lib().pairdiag_dim(h))
+
+
+def pairdiag_nnz(h) -> int:
+    return int(lib().pairdiag_nnz(h))
+
+
+def pairdiag_basis(h) -> np.ndarray:
+    out = np.empty(pairdiag_dim(h), dtype=np.uint64)
+    _check(lib().pairdiag_basis(h, _np_ptr(out)))
+    return out
+
+
+def pairdiag_basis_dev(h, first: int, count: int, out) -> None:
+    import torch
+    _check(lib().pairdiag_basis_dev(h, first, count, _dev_ptr(out, torch.int64)))
+
+
+def pairdiag_rank_dev(h, states, ranks) -> None:
+    import torch
+    _check(lib().pairdiag_rank_dev(h, _dev_ptr(states, torch.int64), states.numel(), _dev_ptr(ranks, torch.int64)))
+
+
+def pairdiag_hx_dev(h, precision: int, x, y) -> None:
+    import torch
+    dt = torch.float64 if precision == PD_PREC_FP64 else torch.float32
+    _check(lib().pairdiag_hx_dev(h, precision, _dev_ptr(x, dt), _dev_ptr(y, dt)))
+
+
+def pairdiag_hx(h, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _check(lib().pairdiag_hx(h, _np_ptr(x), _np_ptr(y)))
+    return y
+
+
+def pairdiag_monopole(h):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    pos = ctypes.c_int64()
+    _check(lib().pairdiag_monopole(h, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(pos)))
+    return lo.value, hi.value, pos.value
+
+
+def pairdiag_set_start(h, v) -> None:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    _check(lib().pairdiag_set_start(h, _np_ptr(v)))
+
+
+def pairdiag_ground_state(h, tol: float, want_vector: bool = True) -> dict:
+    e0 = ctypes.c_double()
+    info = pairdiag_info()
+    vec = np.empty(pairdiag_dim(h), dtype=np.float64) if want_vector else None
+    st = _check(lib().pairdiag_ground_state(h, tol, ctypes.byref(e0), _np_ptr(vec) if want_vector else None,
+                                            ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
+    return dict(e0=e0.value, vec=vec, status=st, **info.as_dict())
+
+
+def pairdiag_ground_state_dev(h, tol: float, vec=None) -> dict:
+    import torch
+    e0 = ctypes.c_double()
+    info = pairdiag_info()
+    st = _check(lib().pairdiag_ground_state_dev(h, tol, ctypes.byref(e0),
+                                                _dev_ptr(vec, torch.float64) if vec is not None else None,
+                                                ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
+    return dict(e0=e0.value, status=st, **info.as_dict())
+
+
+def pairdiag_occupations_dev(h, v, omega: int) -> np.ndarray:
+    """Occupation numbers 2<v|S+_i S-_i|v> of the first ``omega`` orbits."""
+    import torch
+    out = np.empty(64, dtype=np.float64)
+    _check(lib().pairdiag_occupations_dev(h, _dev_ptr(v, torch.float64), _np_ptr(out)))
+    return out[:omega].copy()
+
+
+def pairdiag_multidot(h, Q, ld: int, m: int, p, n: int) -> np.ndarray:
+    import torch
+    dtype = 0 if Q.dtype == torch.float64 else 1
+    out = np.empty(m, dtype=np.float64)
+    _check(lib().pairdiag_multidot(h, dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n, _np_ptr(out)))
+    return out
+
+
+def pairdiag_tridiag_lowest(h, alpha, beta):
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    m = len(alpha)
+    theta = np.empty(2)
+    s = np.empty(m)
+    _check(lib().pairdiag_tridiag_lowest(h, m, _np_ptr(alpha), _np_ptr(beta) if m > 1 else None,
+                                         _np_ptr(theta), _np_ptr(s)))
+    return theta, s
+
+
+# ------------------------------------------------------------ convenience ---
+class Solver:
+    """RAII wrapper: ``with Solver(omega, n, e, G, precision=...) as s: s.ground_state(1e-10)``."""
+
+    def __init__(self, omega: int, n_pairs: int, e, G, **options):
+        self.omega, self.n_pairs = omega, n_pairs
+        self.h = pairdiag_create(omega, n_pairs, e, G, pairdiag_default_options(**options))
+
+    @property
+    def dim(self) -> int:
+        return pairdiag_dim(self.h)
+
+    @property
+    def nnz(self) -> int:
+        return pairdiag_nnz(self.h)
+
+    def ground_state(self, tol: float, want_vector: bool = True) -> dict:
+        return pairdiag_ground_state(self.h, tol, want_vector)
+
+    def close(self):
+        if self.h is not None:
+            pairdiag_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
