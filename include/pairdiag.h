@@ -181,6 +181,21 @@ int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec
  */
 int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ);
 
+/* ------------------------------------------------------- diagnostics ---- */
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * handles, all threads).  Host-side counter; never synchronises. */
+int64_t pairdiag_kernel_launches(void);
+
+/*
+ * Kernel timing of the handle's H*x launches: while enabled (on != 0), every
+ * H*x launch of the handle is bracketed by CUDA events on the handle's stream.
+ * pairdiag_get_profile synchronises the stream, returns the number of timed
+ * launches and their summed duration in milliseconds, and clears the record.
+ */
+int pairdiag_set_profiling(pairdiag_t *h, int on);
+int pairdiag_get_profile(pairdiag_t *h, int64_t *hx_launches, double *hx_ms);
+
 /* ------------------------------------------------ test hooks (device) ---- */
 
 /*

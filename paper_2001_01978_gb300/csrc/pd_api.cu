@@ -20,6 +20,10 @@
 
 using namespace pd;
 
+namespace pd {
+std::atomic<long long> g_kernel_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_last_error = "no error";
@@ -93,12 +97,21 @@ struct pairdiag {
     void *d_p[2] = {nullptr, nullptr};
     double *d_v64 = nullptr, *d_w64 = nullptr;
     std::vector<double> start;
+    // optional event timing of H*x launches
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> hx_events;
+    size_t hx_events_used = 0;
 };
 
 namespace {
 
 void free_all(pairdiag *h)
 {
+    for (auto &ev : h->hx_events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    h->hx_events.clear();
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_counter, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64};
@@ -247,7 +260,19 @@ int ensure_fp64_pair(pairdiag *h)
 int hx(pairdiag *h, int precision, const void *x, void *y)
 {
     HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
+    std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
+    if (h->profiling) {
+        if (h->hx_events_used == h->hx_events.size()) {
+            std::pair<cudaEvent_t, cudaEvent_t> e2;
+            PD_CUDA(cudaEventCreate(&e2.first));
+            PD_CUDA(cudaEventCreate(&e2.second));
+            h->hx_events.push_back(e2);
+        }
+        ev = &h->hx_events[h->hx_events_used++];
+        PD_CUDA(cudaEventRecord(ev->first, h->st));
+    }
     PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_counter, h->hxgrid[precision], h->st));
+    if (ev) PD_CUDA(cudaEventRecord(ev->second, h->st));
     return PD_OK;
 }
 
@@ -283,6 +308,7 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     PD_CUDA(multidot_launch(dtype, Q, dim, 1, Q, dim, h->d_part, &S->dots[0], st));
     PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
     double host_ab[2];
+    std::vector<double> history;                  // |beta_1/alpha_1| per cycle
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
         int used = 0;
         double tnorm = 0.0;
@@ -308,6 +334,11 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
                     cs.converged = true;
                     return PD_OK;
                 }
+                // FP32 vectors: stop once the residual no longer falls (rounding floor);
+                // the caller refines in FP64
+                history.push_back(cs.rel);
+                const size_t nh = history.size();
+                if (dtype == 1 && nh >= 4 && history[nh - 1] > 0.7 * history[nh - 4]) return PD_OK;
             }
             tnorm = std::max(tnorm, std::fabs(a) + b);
             if (i + 1 == m || b <= 1e-13 * tnorm) break;
@@ -573,6 +604,31 @@ void pairdiag_destroy(pairdiag_t *h)
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     free_all(h);
     delete h;
+}
+
+int64_t pairdiag_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+int pairdiag_set_profiling(pairdiag_t *h, int on)
+{
+    if (!h) return fail(PD_EINVAL, "null handle");
+    h->profiling = on != 0;
+    return PD_OK;
+}
+
+int pairdiag_get_profile(pairdiag_t *h, int64_t *hx_launches, double *hx_ms)
+{
+    if (!h || !hx_launches || !hx_ms) return fail(PD_EINVAL, "null argument");
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    double total = 0.0;
+    for (size_t i = 0; i < h->hx_events_used; ++i) {
+        float ms = 0.0f;
+        PD_CUDA(cudaEventElapsedTime(&ms, h->hx_events[i].first, h->hx_events[i].second));
+        total += ms;
+    }
+    *hx_launches = (int64_t)h->hx_events_used;
+    *hx_ms = total;
+    h->hx_events_used = 0;
+    return PD_OK;
 }
 
 int pairdiag_set_stream(pairdiag_t *h, void *stream)

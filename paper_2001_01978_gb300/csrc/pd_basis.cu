@@ -65,6 +65,7 @@ cudaError_t basis_launch(int omega, int n, const uint64_t *binom, int64_t first,
 {
     if (count <= 0) return cudaSuccess;
     basis_kernel<<<grid_for(count), 256, 0, st>>>(omega, n, binom, first, count, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -73,6 +74,7 @@ cudaError_t rank_launch(int omega, int n, const uint64_t *binom, const uint64_t 
 {
     if (count <= 0) return cudaSuccess;
     rank_kernel<<<grid_for(count), 256, 0, st>>>(omega, n, binom, states, count, ranks);
+    count_launches(1);
     return cudaGetLastError();
 }
 

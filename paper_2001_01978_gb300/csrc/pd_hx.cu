@@ -253,6 +253,7 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     if (err != cudaSuccess) return err;
     hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                      static_cast<T *>(y), counter);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -412,6 +413,7 @@ cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials
 {
     monopole_kernel<<<grid, kThreads, 0, st>>>(B, d64, partials);
     monopole_final<<<1, 32, 0, st>>>(partials, grid, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -420,6 +422,7 @@ cudaError_t occupations_launch(const Blocks &B, const double *v, double *partial
 {
     occ_kernel<<<grid, kThreads, 0, st>>>(B, v, partials);
     occ_final<<<1, 64, 0, st>>>(partials, grid, B.omega, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 

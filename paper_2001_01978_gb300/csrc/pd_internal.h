@@ -11,10 +11,15 @@
 // base(h) is the sum of C(L + p_j, ordinal_j) over the set bits of h (ordinals
 // k+1..N).  Both parts are the paper's hash (Sec. 3.2) split at bit L.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace pd {
+
+// kernels launched by the library (diagnostic counter, defined in pd_api.cu)
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launches(int n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int kMaxOmega = 62;
 constexpr int kMaxLow = 13;          // L <= 13: rank table of 2^L uint16 in shared memory

@@ -320,6 +320,7 @@ cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const v
     else
         multidot_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, m, (const float *)p, n, partials);
     reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, m, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -333,6 +334,7 @@ cudaError_t update_launch(int dtype, const void *Q, int64_t ld, int m, const dou
     else
         update_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, m, c, (float *)p, n, part);
     if (norm_out) reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+    count_launches((norm_out ? 2 : 1));
     return cudaGetLastError();
 }
 
@@ -344,18 +346,21 @@ cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const
         scale_kernel<double><<<g, kThreads, 0, st>>>((const double *)src, (double *)dst, n, div, div_is_norm2);
     else
         scale_kernel<float><<<g, kThreads, 0, st>>>((const float *)src, (float *)dst, n, div, div_is_norm2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t finalize_step_launch(LanczosScalars *S, int i, cudaStream_t st)
 {
     finalize_kernel<<<1, 32, 0, st>>>(S, i);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st)
 {
     tridiag_kernel<<<1, 32, 0, st>>>(S, m);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -368,6 +373,7 @@ cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, int m, const double *s, 
     else
         ritz_kernel<float><<<g, kThreads, 0, st>>>((float *)Q, ld, m, s, n, partials);
     reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -376,6 +382,7 @@ cudaError_t random_start_launch(int dtype, void *q, int64_t n, uint64_t seed, cu
     const int g = grid_for(n);
     if (dtype == 0) random_kernel<double><<<g, kThreads, 0, st>>>((double *)q, n, seed);
     else random_kernel<float><<<g, kThreads, 0, st>>>((float *)q, n, seed);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -391,6 +398,7 @@ cudaError_t convert_launch(int dst_dtype, void *dst, int src_dtype, const void *
         convert_kernel<double, double><<<g, kThreads, 0, st>>>((double *)dst, (const double *)src, n);
     else
         convert_kernel<float, float><<<g, kThreads, 0, st>>>((float *)dst, (const float *)src, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -400,6 +408,7 @@ cudaError_t residual_launch(const double *a, const double *b, const double *lamb
     const int g = grid_for(n);
     residual_kernel<<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials);
     reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+    count_launches(2);
     return cudaGetLastError();
 }
 

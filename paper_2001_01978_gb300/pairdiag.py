@@ -67,6 +67,9 @@ _SIGNATURES = {
     "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
+    "pairdiag_kernel_launches": (ctypes.c_int64, []),
+    "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
+    "pairdiag_get_profile": (ctypes.c_int, [_H, _P, _P]),
 }
 
 
@@ -241,6 +244,22 @@ def pairdiag_tridiag_lowest(h, alpha, beta):
     _check(lib().pairdiag_tridiag_lowest(h, m, _np_ptr(alpha), _np_ptr(beta) if m > 1 else None,
                                          _np_ptr(theta), _np_ptr(s)))
     return theta, s
+
+
+def pairdiag_kernel_launches() -> int:
+    return int(lib().pairdiag_kernel_launches())
+
+
+def pairdiag_set_profiling(h, on: bool) -> None:
+    _check(lib().pairdiag_set_profiling(h, 1 if on else 0))
+
+
+def pairdiag_get_profile(h):
+    """(number of timed H*x launches, their summed duration in ms); clears the record."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().pairdiag_get_profile(h, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
 
 
 # ------------------------------------------------------------ convenience ---
