@@ -217,6 +217,35 @@ int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, i
 int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const double *beta,
                             double *theta, double *s);
 
+/*
+ * pairdiag_multidot_noalloc -- the multi-dot of pairdiag_multidot for callers
+ * that cannot allocate device memory.  (The paper has no counterpart: this is
+ * an interface addition of this library.)
+ *
+ * Some callers must not allocate: cudaMalloc and cudaFree can synchronise the
+ * whole device, which a latency-critical host loop cannot afford, and some
+ * host applications give a library no device memory beyond the buffers they
+ * pass in.  This entry point needs no handle and calls no allocating routine:
+ * its partial sums go to a fixed device array inside the library (311,296
+ * bytes, held on every GPU that loads the library until the process exits).
+ *
+ *   out_dev[j] = sum_{i<n} Q_dev[j*ld + i] * p_dev[i],  j < m,  FP64 accumulation
+ *   dtype : 0 = double storage, 1 = float storage (Q and p alike)
+ *   Q_dev, p_dev, out_dev : device pointers; out_dev holds m doubles
+ *   m     : 1..64 (larger m is rejected with PD_EINVAL: the fixed array holds
+ *           partial sums for at most 64 vectors); 0 <= n <= ld
+ *   stream: cudaStream_t as void* (nullptr = legacy default stream)
+ * Asynchronous on `stream`.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) while that device is current; make
+ * that first call before any stream capture begins.  All calls share the one
+ * array and every call overwrites what it reads, so results never depend on an
+ * earlier call -- but calls whose kernels overlap on the GPU (different streams
+ * or threads without ordering between them) race on the array and must be
+ * serialised by the caller.
+ */
+int pairdiag_multidot_noalloc(int dtype, const void *Q_dev, int64_t ld, int m, const void *p_dev,
+                              int64_t n, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -754,6 +755,68 @@ int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const dou
     PD_CUDA(cudaMemcpyAsync(theta, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaMemcpyAsync(s, S->s, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free multi-dot.  Its partial sums live in the file-scope device
+// array below instead of memory obtained from cudaMalloc, so a caller that must
+// not allocate device memory (for example one whose host code runs where a
+// cudaMalloc/cudaFree, with their implicit device-wide synchronisation, is not
+// acceptable, or an application that hands this library no memory beyond the
+// buffers it passes) can still use it.  Every GPU that loads the library holds
+// the array (kNoAllocScratchDoubles doubles, 311,296 bytes) until the process
+// exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocScratchDoubles = 152 * 4 * kMaxWindow;   // one row of kMaxWindow per streaming CTA
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress while that device is current.
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    PD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(PD_ENOTSUP, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(PD_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PD_OK;
+}
+
+}  // namespace
+
+int pairdiag_multidot_noalloc(int dtype, const void *Q_dev, int64_t ld, int m, const void *p_dev, int64_t n,
+                              double *out_dev, void *stream)
+{
+    if (!Q_dev || !p_dev || !out_dev) return fail(PD_EINVAL, "null argument");
+    if (dtype != 0 && dtype != 1) return fail(PD_EINVAL, "dtype must be 0 (double) or 1 (float)");
+    if (m < 1 || m > kMaxWindow)
+        return fail(PD_EINVAL, "m=%d outside 1..%d: the static scratch holds partial sums for at most %d vectors",
+                    m, kMaxWindow, kMaxWindow);
+    if (n < 0 || ld < n) return fail(PD_EINVAL, "need 0 <= n <= ld");
+    if ((int64_t)vec_grid() * kMaxWindow > kNoAllocScratchDoubles)
+        return fail(PD_ENOTSUP, "streaming grid larger than the static scratch");
+    double *scratch = nullptr;
+    PD_TRY(noalloc_scratch(&scratch));
+    // Every partial sum the reduction reads is written by the same call first,
+    // so nothing in the scratch has to start at zero.
+    PD_CUDA(multidot_launch(dtype, Q_dev, ld, m, p_dev, n, scratch, out_dev, static_cast<cudaStream_t>(stream)));
     return PD_OK;
 }
 

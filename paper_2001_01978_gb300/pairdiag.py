@@ -70,6 +70,8 @@ _SIGNATURES = {
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "pairdiag_get_profile": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_multidot_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P,
+                                                 ctypes.c_int64, _P, _P]),
 }
 
 
@@ -233,6 +235,16 @@ def pairdiag_multidot(h, Q, ld: int, m: int, p, n: int) -> np.ndarray:
     out = np.empty(m, dtype=np.float64)
     _check(lib().pairdiag_multidot(h, dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n, _np_ptr(out)))
     return out
+
+
+def pairdiag_multidot_noalloc(Q, ld: int, m: int, p, n: int, out, stream=None) -> None:
+    """Allocation-free multi-dot (no handle): out[j] = Q[j] . p in FP64, written to
+    the device tensor ``out`` (float64, m elements) on ``stream``."""
+    import torch
+    dtype = 0 if Q.dtype == torch.float64 else 1
+    sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().pairdiag_multidot_noalloc(dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n,
+                                           _dev_ptr(out, torch.float64), ctypes.c_void_p(sp)))
 
 
 def pairdiag_tridiag_lowest(h, alpha, beta):
