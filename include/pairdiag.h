@@ -75,6 +75,7 @@ typedef struct {
     int64_t dim;            /* C(Omega, N) */
     int64_t nnz_offdiag;    /* C(Omega,N) * N * (Omega - N) off-diagonal elements (Sec. 5.3) */
     int     iterations;     /* H*x products inside Lanczos (all precisions) */
+    int     hx_products;    /* every H*x product of the call (Lanczos + FP64 refinement) */
     int     iterations_fp32;/* of which with FP32 vectors */
     int     restarts;       /* restart cycles */
     int     converged;      /* 1 if |beta_1/alpha_1| <= tol was reached */
@@ -191,10 +192,11 @@ int64_t pairdiag_kernel_launches(void);
  * Kernel timing of the handle's H*x launches: while enabled (on != 0), every
  * H*x launch of the handle is bracketed by CUDA events on the handle's stream.
  * pairdiag_get_profile synchronises the stream, returns the number of timed
- * launches and their summed duration in milliseconds, and clears the record.
+ * launches of the given precision (PD_PREC_FP64 or PD_PREC_MIXED = FP32) and
+ * their summed duration in milliseconds, and clears the whole record.
  */
 int pairdiag_set_profiling(pairdiag_t *h, int on);
-int pairdiag_get_profile(pairdiag_t *h, int64_t *hx_launches, double *hx_ms);
+int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms);
 
 /* ------------------------------------------------ test hooks (device) ---- */
 

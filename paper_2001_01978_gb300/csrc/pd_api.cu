@@ -101,6 +101,7 @@ struct pairdiag {
     // optional event timing of H*x launches
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> hx_events;
+    std::vector<int> hx_event_prec;
     size_t hx_events_used = 0;
 };
 
@@ -258,7 +259,7 @@ int ensure_fp64_pair(pairdiag *h)
     return PD_OK;
 }
 
-int hx(pairdiag *h, int precision, const void *x, void *y)
+int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nullptr)
 {
     HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
     std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
@@ -268,11 +269,13 @@ int hx(pairdiag *h, int precision, const void *x, void *y)
             PD_CUDA(cudaEventCreate(&e2.first));
             PD_CUDA(cudaEventCreate(&e2.second));
             h->hx_events.push_back(e2);
+            h->hx_event_prec.push_back(0);
         }
+        h->hx_event_prec[h->hx_events_used] = precision;
         ev = &h->hx_events[h->hx_events_used++];
         PD_CUDA(cudaEventRecord(ev->first, h->st));
     }
-    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_counter, h->hxgrid[precision], h->st));
+    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_counter, h->hxgrid[precision], h->st, skip));
     if (ev) PD_CUDA(cudaEventRecord(ev->second, h->st));
     return PD_OK;
 }
@@ -295,8 +298,33 @@ struct CycleStats {
     bool converged = false;
 };
 
+// One Lanczos step i on storage type dtype (Algorithm 2 with full
+// reorthogonalisation, Sec. 3.4): p = H q_i; alpha = q_i^T p; the three-term
+// recurrence p -= alpha q_i + beta_{i-1} q_{i-1} fused with the projections
+// c = Q^T p of one Gram-Schmidt pass against every stored vector; p -= Q c with
+// ||p||^2; then alpha_i = alpha + c_i, beta_i = ||p|| (finalize).  The
+// recurrence followed by the full pass is Gram-Schmidt applied twice.  Every
+// kernel is skipped once S->broken is set (breakdown earlier in the cycle).
+int lanczos_step(pairdiag *h, int dtype, int i)
+{
+    const int64_t dim = h->dim;
+    LanczosScalars *S = h->d_S;
+    const int *skip = &S->broken;
+    void *Q = h->d_Q[dtype];
+    void *p = h->d_p[dtype];
+    cudaStream_t st = h->st;
+    PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip));
+    PD_CUDA(multidot_launch(dtype, qvec(h, dtype, i), dim, 1, p, dim, h->d_part, S->c1, st, skip));
+    PD_CUDA(recur_project_launch(dtype, Q, dim, i, S, p, dim, h->d_part, S->c2, st, skip));
+    PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip));
+    PD_CUDA(finalize_step_launch(S, i, st));
+    return PD_OK;
+}
+
 // Restarted Lanczos on storage type dtype.  Q_0 holds the start vector (any
-// norm).  On return Q_0 is the normalised best vector.
+// norm).  On return Q_0 is the normalised best vector.  The host synchronises
+// once per cycle (to test convergence on the restart vector); breakdown inside
+// a cycle is handled on the device.
 int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &cs)
 {
     const int64_t dim = h->dim;
@@ -305,52 +333,48 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     LanczosScalars *S = h->d_S;
     void *Q = h->d_Q[dtype];
     void *p = h->d_p[dtype];
+    const int *skip = &S->broken;
     // normalise the start vector
     PD_CUDA(multidot_launch(dtype, Q, dim, 1, Q, dim, h->d_part, &S->dots[0], st));
     PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
-    double host_ab[2];
     std::vector<double> history;                  // |beta_1/alpha_1| per cycle
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
-        int used = 0;
-        double tnorm = 0.0;
-        for (int i = 0; i < m; ++i) {
-            PD_TRY(hx(h, dtype, qvec(h, dtype, i), p));
-            ++cs.iterations;
-            PD_CUDA(multidot_launch(dtype, Q, dim, i + 1, p, dim, h->d_part, S->c1, st));
-            PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c1, p, dim, h->d_part, nullptr, st));
-            PD_CUDA(multidot_launch(dtype, Q, dim, i + 1, p, dim, h->d_part, S->c2, st));
-            PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st));
-            PD_CUDA(finalize_step_launch(S, i, st));
-            PD_CUDA(cudaMemcpyAsync(&host_ab[0], &S->alpha[i], sizeof(double), cudaMemcpyDeviceToHost, st));
-            PD_CUDA(cudaMemcpyAsync(&host_ab[1], &S->beta[i], sizeof(double), cudaMemcpyDeviceToHost, st));
-            PD_CUDA(cudaStreamSynchronize(st));
-            used = i + 1;
-            const double a = host_ab[0], b = host_ab[1];
-            if (!std::isfinite(a) || !std::isfinite(b))
-                return fail(PD_ECUDA, "non-finite Lanczos coefficient at step %d", i);
-            if (i == 0) {
-                cs.rel = (b == 0.0) ? 0.0 : b / std::fabs(a);
-                cs.energy = a;
-                if (h->opt.mode == 0 && cs.rel <= tol) {
-                    cs.converged = true;
-                    return PD_OK;
-                }
-                // FP32 vectors: stop once the residual no longer falls (rounding floor);
-                // the caller refines in FP64
-                history.push_back(cs.rel);
-                const size_t nh = history.size();
-                if (dtype == 1 && nh >= 4 && history[nh - 1] > 0.7 * history[nh - 4]) return PD_OK;
+        PD_CUDA(cycle_reset_launch(S, st));
+        PD_TRY(lanczos_step(h, dtype, 0));
+        double ab[2];
+        PD_CUDA(cudaMemcpyAsync(&ab[0], &S->alpha[0], sizeof(double), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaMemcpyAsync(&ab[1], &S->beta[0], sizeof(double), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaStreamSynchronize(st));
+        ++cs.iterations;
+        if (!std::isfinite(ab[0]) || !std::isfinite(ab[1]))
+            return fail(PD_ECUDA, "non-finite Lanczos coefficient in cycle %d", cycle);
+        cs.rel = (ab[1] == 0.0) ? 0.0 : ab[1] / std::fabs(ab[0]);
+        cs.energy = ab[0];
+        if (h->opt.mode == 0) {
+            if (cs.rel <= tol) {
+                cs.converged = true;
+                return PD_OK;
             }
-            tnorm = std::max(tnorm, std::fabs(a) + b);
-            if (i + 1 == m || b <= 1e-13 * tnorm) break;
-            PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i + 1), dim, &S->beta[i], 0, st));
+            // FP32 vectors: stop once the residual no longer falls (rounding floor);
+            // the caller refines in FP64
+            history.push_back(cs.rel);
+            const size_t nh = history.size();
+            if (dtype == 1 && nh >= 4 && history[nh - 1] > 0.7 * history[nh - 4]) return PD_OK;
         }
-        PD_CUDA(tridiag_launch(S, used, st));
-        PD_CUDA(ritz_launch(dtype, Q, dim, used, S->s, dim, h->d_part, &S->norm2, st));
+        for (int i = 1; i < m; ++i) {
+            PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));
+            PD_TRY(lanczos_step(h, dtype, i));
+        }
+        PD_CUDA(tridiag_launch(S, 0, st));
+        PD_CUDA(ritz_launch(dtype, Q, dim, &S->used, S->s, dim, h->d_part, &S->norm2, st));
         PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->norm2, 1, st));
         double th[2];
+        int used = 0;
         PD_CUDA(cudaMemcpyAsync(th, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaMemcpyAsync(&used, &S->used, sizeof(int), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaStreamSynchronize(st));
+        cs.iterations += used - 1;
+        if (!std::isfinite(th[0])) return fail(PD_ECUDA, "non-finite Ritz value in cycle %d", cycle);
         cs.energy = th[0];
         cs.gap = th[1] - th[0];
         if (h->opt.mode == 1) {
@@ -436,6 +460,7 @@ int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool
     CycleStats cs;
     int status = PD_OK;
     int fp32_iters = 0;
+    int refinements = 0;
     int final_dtype = 0;
     double energy = 0.0, rel = INFINITY;
     if (h->opt.precision == PD_PREC_MIXED) {
@@ -446,6 +471,7 @@ int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool
         fp32_iters = cs.iterations;
         double lam, r;
         PD_TRY(rayleigh64(h, 1, &lam, &r));
+        ++refinements;
         energy = lam; rel = r;
         if (r <= tol || h->opt.mode == 1) {
             cs.converged = true;
@@ -475,6 +501,7 @@ int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool
         if (h->opt.mode == 1) {                // report the residual of the Ritz vector
             double lam, r;
             PD_TRY(rayleigh64(h, 0, &lam, &r));
+            ++refinements;
             rel = r;
         }
     }
@@ -495,6 +522,7 @@ int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool
         info->dim = dim;
         info->nnz_offdiag = h->nnz;
         info->iterations = cs.iterations;
+        info->hx_products = cs.iterations + refinements;
         info->iterations_fp32 = fp32_iters;
         info->restarts = cs.restarts;
         info->converged = cs.converged ? 1 : 0;
@@ -616,17 +644,20 @@ int pairdiag_set_profiling(pairdiag_t *h, int on)
     return PD_OK;
 }
 
-int pairdiag_get_profile(pairdiag_t *h, int64_t *hx_launches, double *hx_ms)
+int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms)
 {
     if (!h || !hx_launches || !hx_ms) return fail(PD_EINVAL, "null argument");
     PD_CUDA(cudaStreamSynchronize(h->st));
     double total = 0.0;
+    int64_t count = 0;
     for (size_t i = 0; i < h->hx_events_used; ++i) {
+        if (h->hx_event_prec[i] != precision) continue;
         float ms = 0.0f;
         PD_CUDA(cudaEventElapsedTime(&ms, h->hx_events[i].first, h->hx_events[i].second));
         total += ms;
+        ++count;
     }
-    *hx_launches = (int64_t)h->hx_events_used;
+    *hx_launches = count;
     *hx_ms = total;
     h->hx_events_used = 0;
     return PD_OK;

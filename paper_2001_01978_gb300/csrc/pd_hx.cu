@@ -82,8 +82,10 @@ __device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
 template <typename T, typename A, int R>
 __global__ void __launch_bounds__(kThreads)
 hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
-          const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter)
+          const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
+          const int *__restrict__ skip)
 {
+    if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_next;
     const int omega = B.omega, L = B.L, H = B.H, N = B.n;
@@ -243,7 +245,7 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 
 template <typename T, typename A, int R>
 cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, void *y,
-                     unsigned long long *counter, int grid, cudaStream_t st)
+                     unsigned long long *counter, int grid, cudaStream_t st, const int *skip)
 {
     const size_t smem = layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
     cudaError_t err = cudaFuncSetAttribute(hx_kernel<T, A, R>,
@@ -252,20 +254,20 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (err != cudaSuccess) return err;
     hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                     static_cast<T *>(y), counter);
+                                                     static_cast<T *>(y), counter, skip);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T, typename A>
 cudaError_t launch_prec(const Blocks &B, const A *G, const A *d, const void *x, void *y,
-                        unsigned long long *counter, int grid, cudaStream_t st)
+                        unsigned long long *counter, int grid, cudaStream_t st, const int *skip)
 {
     const int rows = (B.max_block + kThreads - 1) / kThreads;
-    if (rows <= 1) return launch_t<T, A, 1>(B, G, d, x, y, counter, grid, st);
-    if (rows <= 2) return launch_t<T, A, 2>(B, G, d, x, y, counter, grid, st);
-    if (rows <= 4) return launch_t<T, A, 4>(B, G, d, x, y, counter, grid, st);
-    return launch_t<T, A, 8>(B, G, d, x, y, counter, grid, st);
+    if (rows <= 1) return launch_t<T, A, 1>(B, G, d, x, y, counter, grid, st, skip);
+    if (rows <= 2) return launch_t<T, A, 2>(B, G, d, x, y, counter, grid, st, skip);
+    if (rows <= 4) return launch_t<T, A, 4>(B, G, d, x, y, counter, grid, st, skip);
+    return launch_t<T, A, 8>(B, G, d, x, y, counter, grid, st, skip);
 }
 
 template <typename T, typename A>
@@ -401,11 +403,11 @@ int hx_grid(const Blocks &B, int precision)
 }
 
 cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
-                      int *counter, int grid, cudaStream_t st)
+                      int *counter, int grid, cudaStream_t st, const int *skip)
 {
     auto *ctr = reinterpret_cast<unsigned long long *>(counter);
-    if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, ctr, grid, st);
-    return launch_prec<float, float>(B, P.G32, P.d32, x, y, ctr, grid, st);
+    if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, ctr, grid, st, skip);
+    return launch_prec<float, float>(B, P.G32, P.d32, x, y, ctr, grid, st, skip);
 }
 
 cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,

@@ -47,8 +47,9 @@ struct HxProblem {
     const float *G32, *d32;
 };
 size_t hx_smem_bytes(const Blocks &B, int precision);
+// skip (nullable, device): when *skip != 0 the launched kernels return at once
 cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
-                      int *counter, int grid, cudaStream_t st);
+                      int *counter, int grid, cudaStream_t st, const int *skip = nullptr);
 int hx_grid(const Blocks &B, int precision);
 // Monopole_Min/Max/Posit_Min: partials[grid*3] scratch; out[0]=min, out[1]=max, out[2]=pos (as double bits)
 cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,
@@ -73,25 +74,36 @@ struct LanczosScalars {              // lives in device memory
     double theta[2];
     double norm2;
     double dots[4];
-    int    breakdown;
-    int    pad;
+    double tnorm;                    // running max_i |alpha_i| + beta_i + beta_{i-1}
+    int    used;                     // valid Lanczos steps of the current cycle
+    int    broken;                   // breakdown seen: later steps of the cycle are skipped
 };
 int vec_grid();                      // CTAs of the streaming vector kernels
 // partial results of the streaming kernels: [vec_grid() * kMaxWindow] doubles
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
-                            double *partials, double *out, cudaStream_t st);
+                            double *partials, double *out, cudaStream_t st, const int *skip = nullptr);
 // p -= sum_j c[j] Q_j; if norm_out != nullptr also ||p||^2 -> *norm_out
 cudaError_t update_launch(int dtype, const void *Q, int64_t ld, int m, const double *c, void *p,
-                          int64_t n, double *partials, double *norm_out, cudaStream_t st);
+                          int64_t n, double *partials, double *norm_out, cudaStream_t st,
+                          const int *skip = nullptr);
 // dst = src * (1 / sqrt(*norm2)) (or src / *beta when is_norm == 0)
 cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const double *div,
-                         int div_is_norm2, cudaStream_t st);
-// Lanczos step bookkeeping: alpha[i] = c1[i]+c2[i], beta[i] = sqrt(norm2)
+                         int div_is_norm2, cudaStream_t st, const int *skip = nullptr);
+// p <- p - S->c1[0] q_i - S->beta[i-1] q_{i-1} (Algorithm 2 recurrence), then
+// out[j] = Q_j^T p for j <= i (the projections of one full Gram-Schmidt pass)
+cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, const LanczosScalars *S,
+                                 void *p, int64_t n, double *partials, double *out, cudaStream_t st,
+                                 const int *skip = nullptr);
+// Lanczos step bookkeeping: alpha[i] = c1[0]+c2[i], beta[i] = sqrt(norm2), used = i+1;
+// sets broken when beta[i] <= 1e-13 * tnorm (an invariant subspace was found)
 cudaError_t finalize_step_launch(LanczosScalars *S, int i, cudaStream_t st);
-// lowest two eigenvalues + lowest eigenvector of tridiag(alpha, beta) -> S->theta, S->s
+// start of a cycle: used = 0, broken = 0, tnorm = 0
+cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
+// lowest two eigenvalues + lowest eigenvector of tridiag(alpha, beta) -> S->theta, S->s;
+// size m, or S->used when m <= 0
 cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st);
-// Q0 = sum_j s_j Q_j (in place), ||Q0||^2 -> *norm_out
-cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, int m, const double *s, int64_t n,
+// Q0 = sum_j s_j Q_j (in place) for j < *m_dev, ||Q0||^2 -> *norm_out
+cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, const int *m_dev, const double *s, int64_t n,
                         double *partials, double *norm_out, cudaStream_t st);
 cudaError_t random_start_launch(int dtype, void *q, int64_t n, uint64_t seed, cudaStream_t st);
 cudaError_t convert_launch(int dst_dtype, void *dst, int src_dtype, const void *src, int64_t n,

@@ -39,8 +39,9 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 multidot_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p, int64_t n,
-                double *__restrict__ part)
+                double *__restrict__ part, const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     __shared__ double sh[kThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     for (int j0 = 0; j0 < m; j0 += kGroup) {
@@ -63,22 +64,135 @@ multidot_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict
     }
 }
 
-// out[j] = sum_b part[b*kMaxWindow + j], fixed order
-__global__ void reduce_kernel(const double *__restrict__ part, int nb, int m, double *__restrict__ out)
+// Float-float accumulation of exact products with FP32 instructions only:
+// a*b = p + pe exactly (FMA), and (hi, lo) += p + pe with Knuth's TwoSum.  This
+// gives close to FP64 accuracy for dot products of FP32 vectors without FP64
+// arithmetic, which GB300 executes at a small fraction of its FP32 rate.
+__device__ __forceinline__ void ff_add_prod(float &hi, float &lo, float a, float b)
 {
-    const int j = threadIdx.x;
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float t = hi + p;
+    const float z = t - hi;
+    const float e = (hi - (t - z)) + (p - z);
+    hi = t;
+    lo += e + pe;
+}
+
+// multi-dot of FP32 vectors, float-float per thread, FP64 across threads
+__global__ void __launch_bounds__(kThreads)
+multidot_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const float *__restrict__ p, int64_t n,
+                    double *__restrict__ part, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    __shared__ double sh[kThreads / 32];
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int j0 = 0; j0 < m; j0 += kGroup) {
+        float hi[kGroup], lo[kGroup];
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) hi[u] = lo[u] = 0.0f;
+        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
+            const float pv = __ldg(p + i);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m) ff_add_prod(hi[u], lo[u], __ldg(Q + (int64_t)(j0 + u) * ldq + i), pv);
+        }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+            if (j0 + u < m) {
+                const double s = block_sum((double)hi[u] + (double)lo[u], sh);
+                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
+            }
+        }
+    }
+}
+
+// Lanczos recurrence fused with the projections of one Gram-Schmidt pass:
+//   p <- p - alpha q_i - beta_{i-1} q_{i-1}   (Algorithm 2; alpha = S->c1[0])
+//   part <- per-CTA partial sums of Q_j^T p for j <= i (after the update)
+// Elements are visited in the same order by the same thread in every group, so
+// the groups after the first read back this thread's own updated values.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosScalars *__restrict__ S,
+                     T *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    __shared__ double sh[kThreads / 32];
+    const int m = i + 1;
+    const T a = (T)S->c1[0];
+    const T b = (T)(i > 0 ? S->beta[i - 1] : 0.0);
+    const T *qi = Q + (int64_t)i * ldq;
+    const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int j0 = 0; j0 < m; j0 += kGroup) {
+        float hi[kGroup], lo[kGroup];     // used by the FP32 path
+        double acc[kGroup];               // used by the FP64 path
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) { hi[u] = lo[u] = 0.0f; acc[u] = 0.0; }
+        for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n; e += stride) {
+            T v;
+            if (j0 == 0) {
+                v = p[e];
+                if constexpr (sizeof(T) == 4) {
+                    v = fmaf(-a, __ldg(qi + e), v);
+                    if (i > 0) v = fmaf(-b, __ldg(qm + e), v);
+                } else {
+                    v = fma(-a, __ldg(qi + e), v);
+                    if (i > 0) v = fma(-b, __ldg(qm + e), v);
+                }
+                p[e] = v;
+            } else {
+                v = p[e];
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                if (j0 + u < m) {
+                    const T q = __ldg(Q + (int64_t)(j0 + u) * ldq + e);
+                    if constexpr (sizeof(T) == 4) ff_add_prod(hi[u], lo[u], q, v);
+                    else acc[u] = fma((double)q, (double)v, acc[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+            if (j0 + u < m) {
+                const double val = (sizeof(T) == 4) ? (double)hi[u] + (double)lo[u] : acc[u];
+                const double s = block_sum(val, sh);
+                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
+            }
+        }
+    }
+}
+
+// out[j] = sum_b part[b*kMaxWindow + j]: one warp per output, each lane a fixed
+// strided subset, then a fixed xor-shuffle tree (deterministic)
+__global__ void reduce_kernel(const double *__restrict__ part, int nb, int m, double *__restrict__ out,
+                              const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (j >= m) return;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b * kMaxWindow + j];
-    out[j] = s;
+#pragma unroll 4
+    for (int b = lane; b < nb; b += 32) s += part[b * kMaxWindow + j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[j] = s;
+}
+
+inline void reduce(const double *part, int nb, int m, double *out, cudaStream_t st, const int *skip = nullptr)
+{
+    reduce_kernel<<<(m + 7) / 8, 256, 0, st>>>(part, nb, m, out, skip);
 }
 
 // p -= sum_j c_j Q_j ; optional ||p||^2 partials (of the stored, rounded values)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 update_kernel(const T *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ c,
-              T *__restrict__ p, int64_t n, double *__restrict__ part)
+              T *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     __shared__ double sc[kMaxWindow];
     __shared__ double sh[kThreads / 32];
     for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = c[j];
@@ -98,10 +212,47 @@ update_kernel(const T *__restrict__ Q, int64_t ldq, int m, const double *__restr
     }
 }
 
+// p -= sum_j c_j Q_j with FP32 FMAs (the result is stored in FP32 anyway; the
+// second Gram-Schmidt pass removes what this rounding leaves along Q)
+__global__ void __launch_bounds__(kThreads)
+update_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ c,
+                  float *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    __shared__ float sc[kMaxWindow];
+    __shared__ double sh[kThreads / 32];
+    for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = (float)c[j];
+    __syncthreads();
+    float hi = 0.0f, lo = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
+        float v = p[i];
+        for (int j = 0; j < m; ++j) v = fmaf(-sc[j], __ldg(Q + (int64_t)j * ldq + i), v);
+        p[i] = v;
+        ff_add_prod(hi, lo, v, v);
+    }
+    if (part) {
+        const double s = block_sum((double)hi + (double)lo, sh);
+        if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
+    }
+}
+
+__global__ void scale_f32_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t n,
+                                 const double *__restrict__ div, int is_norm2, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const double d = is_norm2 ? sqrt(*div) : *div;
+    const float f = (d > 0.0) ? (float)(1.0 / d) : 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = src[i] * f;
+}
+
 template <typename T>
 __global__ void scale_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t n,
-                             const double *__restrict__ div, int is_norm2)
+                             const double *__restrict__ div, int is_norm2, const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     const double d = is_norm2 ? sqrt(*div) : *div;
     const double f = (d > 0.0) ? 1.0 / d : 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -111,9 +262,24 @@ __global__ void scale_kernel(const T *__restrict__ src, T *__restrict__ dst, int
 
 __global__ void finalize_kernel(LanczosScalars *S, int i)
 {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || S->broken) return;
+    const double a = S->c1[0] + S->c2[i];
+    const double b = sqrt(S->norm2);
+    S->alpha[i] = a;
+    S->beta[i] = b;
+    const double row = fabs(a) + b + (i > 0 ? S->beta[i - 1] : 0.0);
+    const double tn = fmax(S->tnorm, row);
+    S->tnorm = tn;
+    S->used = i + 1;
+    if (!(b > 1e-13 * tn)) S->broken = 1;        // invariant subspace found (or a NaN)
+}
+
+__global__ void cycle_reset_kernel(LanczosScalars *S)
+{
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    S->alpha[i] = S->c1[i] + S->c2[i];
-    S->beta[i] = sqrt(S->norm2);
+    S->used = 0;
+    S->broken = 0;
+    S->tnorm = 0.0;
 }
 
 // ---- symmetric tridiagonal eigenproblem (one warp) --------------------------
@@ -192,6 +358,8 @@ __global__ void tridiag_kernel(LanczosScalars *S, int m)
     __shared__ double a[kMaxWindow], b[kMaxWindow], b2[kMaxWindow];
     __shared__ double z[kMaxWindow], u0[kMaxWindow], u1[kMaxWindow], u2[kMaxWindow];
     const int lane = threadIdx.x;
+    if (m <= 0) m = S->used;
+    if (m < 1 || m > kMaxWindow) return;
     for (int i = lane; i < m; i += 32) {
         a[i] = S->alpha[i];
         b[i] = (i + 1 < m) ? S->beta[i] : 0.0;
@@ -236,9 +404,10 @@ __global__ void tridiag_kernel(LanczosScalars *S, int m)
 // Q0 <- sum_j s_j Q_j (in place; each element is read before it is written)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-ritz_kernel(T *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ s, int64_t n,
-            double *__restrict__ part)
+ritz_kernel(T *__restrict__ Q, int64_t ldq, const int *__restrict__ m_dev, const double *__restrict__ s,
+            int64_t n, double *__restrict__ part)
 {
+    const int m = *m_dev;
     __shared__ double ss[kMaxWindow];
     __shared__ double sh[kThreads / 32];
     for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = s[j];
@@ -253,6 +422,27 @@ ritz_kernel(T *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ s,
         nrm += (double)t * (double)t;
     }
     const double sum = block_sum(nrm, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = sum;
+}
+
+__global__ void __launch_bounds__(kThreads)
+ritz_f32_kernel(float *__restrict__ Q, int64_t ldq, const int *__restrict__ m_dev, const double *__restrict__ s,
+                int64_t n, double *__restrict__ part)
+{
+    const int m = *m_dev;
+    __shared__ float ss[kMaxWindow];
+    __shared__ double sh[kThreads / 32];
+    for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = (float)s[j];
+    __syncthreads();
+    float hi = 0.0f, lo = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
+        float v = 0.0f;
+        for (int j = 0; j < m; ++j) v = fmaf(ss[j], Q[(int64_t)j * ldq + i], v);
+        Q[i] = v;
+        ff_add_prod(hi, lo, v, v);
+    }
+    const double sum = block_sum((double)hi + (double)lo, sh);
     if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = sum;
 }
 
@@ -312,47 +502,68 @@ int grid_for(int64_t n)
 int vec_grid() { return kGrid; }
 
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
-                            double *partials, double *out, cudaStream_t st)
+                            double *partials, double *out, cudaStream_t st, const int *skip)
 {
     const int g = grid_for(n);
     if (dtype == 0)
-        multidot_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, (const double *)p, n, partials);
+        multidot_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, (const double *)p, n, partials, skip);
     else
-        multidot_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, m, (const float *)p, n, partials);
-    reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, m, out);
+        multidot_f32_kernel<<<g, kThreads, 0, st>>>((const float *)Q, ld, m, (const float *)p, n, partials, skip);
+    reduce(partials, g, m, out, st, skip);
     count_launches(2);
     return cudaGetLastError();
 }
 
 cudaError_t update_launch(int dtype, const void *Q, int64_t ld, int m, const double *c, void *p,
-                          int64_t n, double *partials, double *norm_out, cudaStream_t st)
+                          int64_t n, double *partials, double *norm_out, cudaStream_t st, const int *skip)
 {
     const int g = grid_for(n);
     double *part = norm_out ? partials : nullptr;
     if (dtype == 0)
-        update_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, c, (double *)p, n, part);
+        update_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, c, (double *)p, n, part, skip);
     else
-        update_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, m, c, (float *)p, n, part);
-    if (norm_out) reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+        update_f32_kernel<<<g, kThreads, 0, st>>>((const float *)Q, ld, m, c, (float *)p, n, part, skip);
+    if (norm_out) reduce(partials, g, 1, norm_out, st, skip);
     count_launches((norm_out ? 2 : 1));
     return cudaGetLastError();
 }
 
 cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const double *div,
-                         int div_is_norm2, cudaStream_t st)
+                         int div_is_norm2, cudaStream_t st, const int *skip)
 {
     const int g = grid_for(n);
     if (dtype == 0)
-        scale_kernel<double><<<g, kThreads, 0, st>>>((const double *)src, (double *)dst, n, div, div_is_norm2);
+        scale_kernel<double><<<g, kThreads, 0, st>>>((const double *)src, (double *)dst, n, div, div_is_norm2, skip);
     else
-        scale_kernel<float><<<g, kThreads, 0, st>>>((const float *)src, (float *)dst, n, div, div_is_norm2);
+        scale_f32_kernel<<<g, kThreads, 0, st>>>((const float *)src, (float *)dst, n, div, div_is_norm2, skip);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, const LanczosScalars *S,
+                                 void *p, int64_t n, double *partials, double *out, cudaStream_t st,
+                                 const int *skip)
+{
+    const int g = grid_for(n);
+    if (dtype == 0)
+        recur_project_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, i, S, (double *)p, n, partials, skip);
+    else
+        recur_project_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, i, S, (float *)p, n, partials, skip);
+    reduce(partials, g, i + 1, out, st, skip);
+    count_launches(2);
     return cudaGetLastError();
 }
 
 cudaError_t finalize_step_launch(LanczosScalars *S, int i, cudaStream_t st)
 {
     finalize_kernel<<<1, 32, 0, st>>>(S, i);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st)
+{
+    cycle_reset_kernel<<<1, 32, 0, st>>>(S);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -364,15 +575,15 @@ cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, int m, const double *s, int64_t n,
+cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, const int *m_dev, const double *s, int64_t n,
                         double *partials, double *norm_out, cudaStream_t st)
 {
     const int g = grid_for(n);
     if (dtype == 0)
-        ritz_kernel<double><<<g, kThreads, 0, st>>>((double *)Q, ld, m, s, n, partials);
+        ritz_kernel<double><<<g, kThreads, 0, st>>>((double *)Q, ld, m_dev, s, n, partials);
     else
-        ritz_kernel<float><<<g, kThreads, 0, st>>>((float *)Q, ld, m, s, n, partials);
-    reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+        ritz_f32_kernel<<<g, kThreads, 0, st>>>((float *)Q, ld, m_dev, s, n, partials);
+    reduce(partials, g, 1, norm_out, st);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -407,7 +618,7 @@ cudaError_t residual_launch(const double *a, const double *b, const double *lamb
 {
     const int g = grid_for(n);
     residual_kernel<<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials);
-    reduce_kernel<<<1, kMaxWindow, 0, st>>>(partials, g, 1, norm_out);
+    reduce(partials, g, 1, norm_out, st);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -27,7 +27,7 @@ class pairdiag_options(ctypes.Structure):
 
 class pairdiag_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int64), ("nnz_offdiag", ctypes.c_int64), ("iterations", ctypes.c_int),
-                ("iterations_fp32", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("hx_products", ctypes.c_int), ("iterations_fp32", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("gap_estimate", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
@@ -69,7 +69,7 @@ _SIGNATURES = {
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
-    "pairdiag_get_profile": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_multidot_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P,
                                                  ctypes.c_int64, _P, _P]),
 }
@@ -266,11 +266,12 @@ def pairdiag_set_profiling(h, on: bool) -> None:
     _check(lib().pairdiag_set_profiling(h, 1 if on else 0))
 
 
-def pairdiag_get_profile(h):
-    """(number of timed H*x launches, their summed duration in ms); clears the record."""
+def pairdiag_get_profile(h, precision: int = PD_PREC_MIXED):
+    """(number of timed H*x launches of this precision, their summed duration in
+    ms); clears the whole record."""
     n = ctypes.c_int64()
     ms = ctypes.c_double()
-    _check(lib().pairdiag_get_profile(h, ctypes.byref(n), ctypes.byref(ms)))
+    _check(lib().pairdiag_get_profile(h, precision, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
 
 
