@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--omega", type=int, default=0, help="with --hx-only: picket-fence size instead of --workload")
     ap.add_argument("--npairs", type=int, default=0)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--hx-variant", type=int, default=0, help="H*x kernel variant (0 = automatic)")
+    ap.add_argument("--low-bits", type=int, default=0, help="orbits per basis block (0 = automatic)")
     return ap.parse_args()
 
 
@@ -232,7 +234,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def make(prec):
-        s = pd.Solver(omega, n, e, G, precision=prec, window=args.window, start=pd.PD_START_RANDOM, seed=1)
+        s = pd.Solver(omega, n, e, G, precision=prec, window=args.window, start=pd.PD_START_RANDOM, seed=1,
+                      hx_variant=args.hx_variant, low_bits=args.low_bits)
         pd.pairdiag_set_stream(s.h, stream)
         return s
 
@@ -393,7 +396,7 @@ def run_hx_only(args):
     prec = pd.PD_PREC_MIXED if args.precision == "fp32" else pd.PD_PREC_FP64
     dt = torch.float32 if prec == pd.PD_PREC_MIXED else torch.float64
     es = 4 if prec == pd.PD_PREC_MIXED else 8
-    with pd.Solver(omega, n, e, G) as s:
+    with pd.Solver(omega, n, e, G, hx_variant=args.hx_variant, low_bits=args.low_bits) as s:
         stream = torch.cuda.current_stream()
         pd.pairdiag_set_stream(s.h, stream)
         g = torch.Generator(device="cuda").manual_seed(1)
@@ -415,6 +418,7 @@ def run_hx_only(args):
     alg = nnz * es + 2 * dim * es
     peak, kind = measured_peaks()
     print(json.dumps({"hx_only": True, "workload": name, "precision": args.precision, "dim": dim,
+                      "hx_variant": args.hx_variant, "low_bits": args.low_bits,
                       "nnz": nnz, "median_ms": ms, "min_ms": min(times), "nnz_per_s": nnz / (ms * 1e-3),
                       "alg_gbs": alg / (ms * 1e-3) / 1e9, "frac_of_" + kind + "_hbm": alg / (ms * 1e-3) / 1e9 / peak,
                       "l2": "flushed before each launch"}))

@@ -69,6 +69,9 @@ typedef struct {
     int      low_bits;      /* orbits handled inside one basis block (0 = automatic) */
     double   mixed_floor;   /* relative residual at which FP32 cycles hand over to FP64
                                refinement (PD_PREC_MIXED only); default 5e-6 */
+    int      hx_variant;    /* H*x kernel: 0 = automatic (default, currently 1), 1 = neighbour
+                               blocks staged one at a time, 2 = all neighbour blocks staged at
+                               once (falls back to 1 when its shared memory does not fit) */
 } pairdiag_options;
 
 typedef struct {

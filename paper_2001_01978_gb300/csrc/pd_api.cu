@@ -225,6 +225,7 @@ int build_tables(pairdiag *h)
     B.nblocks = (int64_t)hw.size();
     B.max_block = max_block;
     B.max_hh = max_hh;
+    B.variant = h->opt.hx_variant;
     B.blk_h = h->d_blk_h; B.blk_base = h->d_blk_base;
     B.lowword = h->d_lowword; B.rankL = h->d_rankL; B.binom = h->d_binom;
     for (int k = 0; k <= kMaxLow + 1; ++k) B.lo_off[k] = (k <= L + 1) ? off[k] : off[L + 1];
@@ -548,6 +549,7 @@ void pairdiag_default_options(pairdiag_options *opt)
     opt->mode = 0;
     opt->low_bits = 0;
     opt->mixed_floor = 5e-6;
+    opt->hx_variant = 0;
 }
 
 const char *pairdiag_strerror(int code)
@@ -589,6 +591,7 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     if (o.mode != 0 && o.mode != 1) return fail(PD_EINVAL, "bad mode");
     if (o.low_bits < 0 || o.low_bits > kMaxLow) return fail(PD_EINVAL, "low_bits outside 0..%d", kMaxLow);
     if (o.max_restarts < 0) return fail(PD_EINVAL, "max_restarts < 0");
+    if (o.hx_variant < 0 || o.hx_variant > 2) return fail(PD_EINVAL, "hx_variant outside 0..2");
 
     pairdiag *h = new pairdiag();
     h->omega = omega; h->n = n_pairs; h->opt = o;

@@ -243,18 +243,275 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     }
 }
 
+// ---- variant 2: every neighbouring block of the high<->low hops staged at once --
+struct Layout2 {
+    size_t gl, gs, ge, d, rank, x, xn, ud, hh, occ, emp, total;
+};
+
+template <typename T, typename A>
+__host__ __device__ inline Layout2 layout2(int omega, int L, int H, int max_block, int max_hh)
+{
+    Layout2 s;
+    size_t off = 0;
+    const int h1 = H > 0 ? H : 1;
+    s.gl = off;   off = align16(off + sizeof(A) * L * L);
+    s.gs = off;   off = align16(off + sizeof(A) * h1 * L);
+    s.ge = off;   off = align16(off + sizeof(A) * h1 * L);
+    s.d = off;    off = align16(off + sizeof(A) * omega);
+    s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
+    s.x = off;    off = align16(off + sizeof(T) * max_block);
+    s.xn = off;   off = align16(off + sizeof(T) * (size_t)h1 * max_block);
+    s.ud = off;   off = align16(off + sizeof(uint16_t) * (size_t)L * max_block);
+    s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
+    s.occ = off;  off = align16(off + sizeof(uint64_t) * h1);
+    s.emp = off;  off = align16(off + sizeof(uint64_t) * h1);
+    s.total = off;
+    return s;
+}
+
+// Same product as hx_kernel.  Differences: all ph blocks h - o (k+1 low pairs)
+// and all H-ph blocks h + e (k-1) are staged together behind one barrier; each
+// row's neighbour ranks rank(l + e) and rank(l - o) are computed once per block
+// and kept packed (rank << 4 | orbit) in shared memory; the coefficients of the
+// high<->low hops are laid out per staged block (G_{e, L+t} for block h - t at
+// row t of sGS, G_{L+t, o} for block h + t in sGE), so the innermost loop runs
+// over the staged blocks with one coefficient load, one gather and one FMA.
+template <typename T, typename A, int R>
+__global__ void __launch_bounds__(kThreads)
+hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
+           const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
+           const int *__restrict__ skip)
+{
+    if (skip && *skip) return;                    // CTA-uniform
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_next;
+    const int omega = B.omega, L = B.L, H = B.H, N = B.n, MB = B.max_block;
+    const Layout2 lay = layout2<T, A>(omega, L, H, MB, B.max_hh);
+    A *sGL = reinterpret_cast<A *>(smem + lay.gl);
+    A *sGS = reinterpret_cast<A *>(smem + lay.gs);
+    A *sGE = reinterpret_cast<A *>(smem + lay.ge);
+    A *sd = reinterpret_cast<A *>(smem + lay.d);
+    uint16_t *sRank = reinterpret_cast<uint16_t *>(smem + lay.rank);
+    T *sx = reinterpret_cast<T *>(smem + lay.x);
+    T *sxn = reinterpret_cast<T *>(smem + lay.xn);
+    uint16_t *sUD = reinterpret_cast<uint16_t *>(smem + lay.ud);
+    HHop<A> *sHH = reinterpret_cast<HHop<A> *>(smem + lay.hh);
+    uint64_t *sOccB = reinterpret_cast<uint64_t *>(smem + lay.occ);
+    uint64_t *sEmpB = reinterpret_cast<uint64_t *>(smem + lay.emp);
+    const int tid = threadIdx.x;
+
+    for (int i = tid; i < L * L; i += kThreads) sGL[i] = Gg[(i / L) * omega + (i % L)];
+    for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
+    for (int i = tid; i < (1 << L); i += kThreads) sRank[i] = B.rankL[i];
+    const uint32_t maskL = (1u << L) - 1u;
+    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
+
+    for (;;) {
+        __syncthreads();                          // smem of the previous block is free
+        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long b = s_next;
+        if (b >= B.nblocks) break;
+
+        const uint64_t h = __ldg(B.blk_h + b);
+        const uint64_t base = __ldg(B.blk_base + b);
+        const int ph = __popcll(h);
+        const int k = N - ph;
+        const int nk = (int)__ldg(B.binom + L * kBinomStride + k);
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        const int nemp = H - ph;
+        const int nhh = ph * nemp;
+        const int n_up = (k < L) ? (int)__ldg(B.binom + L * kBinomStride + k + 1) : 0;
+        const int n_dn = (k > 0) ? (int)__ldg(B.binom + L * kBinomStride + k - 1) : 0;
+        T *sxd = sxn + ph * n_up;                 // staged blocks h + e start here
+
+        for (int t = tid; t < nhh; t += kThreads) {
+            const int a = t / nemp, c = t - a * nemp;
+            const int o = nth_set_bit(h, a);
+            const int q = nth_set_bit(~h & maskH, c);
+            sHH[t].base = block_base(h ^ (1ull << o) ^ (1ull << q), L, N, B.binom);
+            sHH[t].g = Gg[(L + q) * omega + (L + o)];
+        }
+        for (int t = tid; t < H; t += kThreads) {
+            const uint64_t bit = 1ull << t;
+            if (h & bit) {
+                const int j = __popcll(h & (bit - 1));
+                sOccB[j] = n_up ? block_base(h ^ bit, L, N, B.binom) : 0;
+                for (int e = 0; e < L; ++e) sGS[j * L + e] = Gg[e * omega + L + t];
+            } else {
+                const int j = __popcll(~h & maskH & (bit - 1));
+                sEmpB[j] = n_dn ? block_base(h | bit, L, N, B.binom) : 0;
+                for (int o = 0; o < L; ++o) sGE[j * L + o] = Gg[(L + t) * omega + o];
+            }
+        }
+        for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
+        __syncthreads();                          // slot bases visible
+
+        if (n_up)
+            for (int j = 0; j < ph; ++j) {
+                const T *src = x + sOccB[j];
+                T *dst = sxn + j * n_up;
+                for (int r = tid; r < n_up; r += kThreads) dst[r] = src[r];
+            }
+        if (n_dn)
+            for (int j = 0; j < nemp; ++j) {
+                const T *src = x + sEmpB[j];
+                T *dst = sxd + j * n_dn;
+                for (int r = tid; r < n_dn; r += kThreads) dst[r] = src[r];
+            }
+
+        A Dh = A(0);
+        for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
+
+        uint32_t lr[R];
+        A acc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            lr[i] = 0;
+            acc[i] = A(0);
+            if (r < nk) {
+                const uint32_t l = lw[r];
+                lr[i] = l;
+                A D = A(0);
+                for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
+                acc[i] = (D + Dh) * A(sx[r]);
+                // neighbour ranks of this row: up (l + e) then down (l - o); only
+                // this thread reads them back
+                int slot = 0;
+                for (uint32_t w = ~l & maskL; w; w &= w - 1, ++slot) {
+                    const int e = __ffs(w) - 1;
+                    sUD[slot * MB + r] = (uint16_t)((sRank[l | (1u << e)] << 4) | e);
+                }
+                for (uint32_t w = l; w; w &= w - 1, ++slot) {
+                    const int o = __ffs(w) - 1;
+                    sUD[slot * MB + r] = (uint16_t)((sRank[l ^ (1u << o)] << 4) | o);
+                }
+            }
+        }
+
+        // low -> low
+        if (k > 0 && k < L) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (tid + i * kThreads < nk) {
+                    const uint32_t l = lr[i];
+                    A a = acc[i];
+                    uint32_t occ = l;
+                    for (int u = 0; u < k; ++u) {
+                        const int o = __ffs(occ) - 1;
+                        occ &= occ - 1;
+                        const uint32_t lo = l ^ (1u << o);
+                        const A *gcol = sGL + o;
+                        uint32_t emp = ~l & maskL;
+                        for (int v = 0; v < L - k; ++v) {
+                            const int q = __ffs(emp) - 1;
+                            emp &= emp - 1;
+                            a += gcol[q * L] * A(sx[sRank[lo | (1u << q)]]);
+                        }
+                    }
+                    acc[i] = a;
+                }
+            }
+        }
+
+        // high -> high: same offsets in the target block
+        for (int j = 0; j < nhh; ++j) {
+            const T *xb = x + sHH[j].base;
+            const A g = sHH[j].g;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = tid + i * kThreads;
+                if (r < nk) acc[i] += g * A(__ldg(xb + r));
+            }
+        }
+        __syncthreads();                          // staged neighbour blocks visible
+
+        // high -> low: pair from occupied high orbit L+t to empty low orbit e
+        if (n_up) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = tid + i * kThreads;
+                if (r < nk) {
+                    A a = acc[i];
+                    for (int v = 0; v < L - k; ++v) {
+                        const uint32_t pk = sUD[v * MB + r];
+                        const A *g = sGS + (pk & 15u);
+                        const T *xp = sxn + (pk >> 4);
+                        for (int j = 0; j < ph; ++j) a += g[j * L] * A(xp[j * n_up]);
+                    }
+                    acc[i] = a;
+                }
+            }
+        }
+        // low -> high: pair from occupied low orbit o to empty high orbit L+t
+        if (n_dn) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = tid + i * kThreads;
+                if (r < nk) {
+                    A a = acc[i];
+                    for (int u = 0; u < k; ++u) {
+                        const uint32_t pk = sUD[(L - k + u) * MB + r];
+                        const A *g = sGE + (pk & 15u);
+                        const T *xp = sxd + (pk >> 4);
+                        for (int j = 0; j < nemp; ++j) a += g[j * L] * A(xp[j * n_dn]);
+                    }
+                    acc[i] = a;
+                }
+            }
+        }
+
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) y[base + r] = T(acc[i]);
+        }
+    }
+}
+
+constexpr size_t kSmemLimit = 200 * 1024;
+
+// Variant 2 only on request (and when its shared memory fits): measured on
+// GB300 it is slower than variant 1 (0.40 vs 0.30 ms at Omega=24, 157 vs 99 ms at
+// Omega=32 in FP32) because its shared-memory footprint leaves 1-2 CTAs per SM.
+template <typename T, typename A>
+bool use_v2(const Blocks &B)
+{
+    if (B.variant != 2) return false;
+    return layout2<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total <= kSmemLimit;
+}
+
+template <typename T, typename A, int R>
+const void *kernel_fn(const Blocks &B)
+{
+    return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R>;
+}
+
+template <typename T, typename A>
+size_t kernel_smem(const Blocks &B)
+{
+    return use_v2<T, A>(B) ? layout2<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total
+                           : layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+}
+
 template <typename T, typename A, int R>
 cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, void *y,
                      unsigned long long *counter, int grid, cudaStream_t st, const int *skip)
 {
-    const size_t smem = layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
-    cudaError_t err = cudaFuncSetAttribute(hx_kernel<T, A, R>,
+    const size_t smem = kernel_smem<T, A>(B);
+    const bool v2 = use_v2<T, A>(B);
+    cudaError_t err = cudaFuncSetAttribute(kernel_fn<T, A, R>(B),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (err != cudaSuccess) return err;
-    hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                     static_cast<T *>(y), counter, skip);
+    if (v2)
+        hx2_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                          static_cast<T *>(y), counter, skip);
+    else
+        hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                         static_cast<T *>(y), counter, skip);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -273,12 +530,12 @@ cudaError_t launch_prec(const Blocks &B, const A *G, const A *d, const void *x, 
 template <typename T, typename A>
 int grid_prec(const Blocks &B)
 {
-    const size_t smem = layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+    const size_t smem = kernel_smem<T, A>(B);
     const int rows = (B.max_block + kThreads - 1) / kThreads;
-    const void *fn = rows <= 1 ? (const void *)hx_kernel<T, A, 1>
-                   : rows <= 2 ? (const void *)hx_kernel<T, A, 2>
-                   : rows <= 4 ? (const void *)hx_kernel<T, A, 4>
-                               : (const void *)hx_kernel<T, A, 8>;
+    const void *fn = rows <= 1 ? kernel_fn<T, A, 1>(B)
+                   : rows <= 2 ? kernel_fn<T, A, 2>(B)
+                   : rows <= 4 ? kernel_fn<T, A, 4>(B)
+                               : kernel_fn<T, A, 8>(B);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -393,8 +650,12 @@ __global__ void occ_final(const double *__restrict__ part, int n, int omega, dou
 
 size_t hx_smem_bytes(const Blocks &B, int precision)
 {
-    return precision == 0 ? layout<double, double>(B.omega, B.L, B.H, B.max_block, B.max_hh).total
-                          : layout<float, float>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
+    return precision == 0 ? kernel_smem<double, double>(B) : kernel_smem<float, float>(B);
+}
+
+int hx_variant(const Blocks &B, int precision)
+{
+    return (precision == 0 ? use_v2<double, double>(B) : use_v2<float, float>(B)) ? 2 : 1;
 }
 
 int hx_grid(const Blocks &B, int precision)

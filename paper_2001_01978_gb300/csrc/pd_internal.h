@@ -37,6 +37,7 @@ struct Blocks {
     const uint16_t *rankL;           // [2^L] rank of a word within its popcount group
     const uint64_t *binom;           // [64*64]
     int lo_off[kMaxLow + 2];         // group offsets into lowword
+    int variant;                     // H*x kernel: 0 automatic, 1 staged per neighbour, 2 all staged
 };
 
 // ---- H*x (pd_hx.cu) -------------------------------------------------------
@@ -47,6 +48,7 @@ struct HxProblem {
     const float *G32, *d32;
 };
 size_t hx_smem_bytes(const Blocks &B, int precision);
+int hx_variant(const Blocks &B, int precision);   // kernel variant a launch will use (1 or 2)
 // skip (nullable, device): when *skip != 0 the launched kernels return at once
 cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
                       int *counter, int grid, cudaStream_t st, const int *skip = nullptr);

@@ -22,7 +22,7 @@ PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER = 0, 1, 2, 3
 class pairdiag_options(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("max_restarts", ctypes.c_int), ("precision", ctypes.c_int),
                 ("start", ctypes.c_int), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
-                ("low_bits", ctypes.c_int), ("mixed_floor", ctypes.c_double)]
+                ("low_bits", ctypes.c_int), ("mixed_floor", ctypes.c_double), ("hx_variant", ctypes.c_int)]
 
 
 class pairdiag_info(ctypes.Structure):

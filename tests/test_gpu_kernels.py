@@ -135,6 +135,27 @@ def test_hx_fp32_vs_oracle(omega, n, low):
         assert np.all(np.abs(got - ref) <= bound)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("omega,n,low", [(16, 5, 0), (20, 10, 0), (19, 9, 3), (15, 7, 8), (22, 4, 0), (24, 12, 13)])
+def test_hx_variants_vs_oracle(omega, n, low, variant):
+    """Both H*x kernel variants (neighbour blocks staged one at a time / all at once)."""
+    e, G = pd_inputs.separable_noise(omega, seed=omega + 7 * n)
+    b = oracle.basis(omega, n)
+    x = pd_inputs.random_vector(len(b), omega + n)
+    ref = oracle.hx(omega, n, e, G, x, b)
+    scale = abs_row_scale(omega, n, e, G, x, basis=b)
+    with pd.Solver(omega, n, e, G, low_bits=low, hx_variant=variant) as s:
+        got = pd.pairdiag_hx(s.h, x)
+        assert np.all(np.abs(got - ref) <= hx_bound(omega, n, scale, EPS64))
+        xt = torch.from_numpy(x.astype(np.float32)).cuda()
+        yt = torch.empty_like(xt)
+        pd.pairdiag_hx_dev(s.h, pd.PD_PREC_MIXED, xt, yt)
+        x32 = x.astype(np.float32).astype(np.float64)
+        ref32 = oracle.hx(omega, n, e, G, x32, b)
+        scale32 = abs_row_scale(omega, n, e, G, x32, basis=b)
+        assert np.all(np.abs(yt.cpu().numpy() - ref32) <= hx_bound(omega, n, scale32, EPS32))
+
+
 def test_hx_dev_fp64_and_stream():
     omega, n = 20, 9
     e, G = pd_inputs.constant_noise(omega, seed=5)
