@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--hx-variant", type=int, default=0, help="H*x kernel variant (0 = automatic)")
     ap.add_argument("--low-bits", type=int, default=0, help="orbits per basis block (0 = automatic)")
+    ap.add_argument("--batch", action="store_true",
+                    help="4096-problem mean-field workload: solves/s and per-solve latency (own JSON line)")
+    ap.add_argument("--batch-count", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -425,8 +428,52 @@ def run_hx_only(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form: 4096 Hamiltonians (Omega ~ U{10..22}, N = Omega/2 +- U{0..3}) in
+    one lock-step solve, mixed form vs plain FP64, same tolerance."""
+    import torch
+    import paper_2001_01978_gb300 as pd
+    torch.cuda.set_device(0)
+    probs = pd_inputs.batch_workload(args.batch_count, seed=5)
+    dims = [math.comb(om, n) for om, n, _, _ in probs]
+    nnz = sum(d * n * (om - n) for d, (om, n, _, _) in zip(dims, probs))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec in (("mixed", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
+        opt = pd.pairdiag_default_options(precision=prec, window=args.window)
+        for _ in range(max(1, args.warmup // 3)):
+            pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream)
+        times, res = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            res = pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        ms = statistics.median(times)
+        lat = res["latency_ms"]
+        iters = res["iterations"]
+        out[name] = {"batch_ms": ms, "solves_per_s": len(probs) / (ms * 1e-3),
+                     "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                     "converged_frac": float(np.mean(res["converged"])),
+                     "iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
+                     "e0_first": float(res["e0"][0])}
+    e_m = np.array([0.0])
+    print(json.dumps({"batch": True, "workload": "mean-field batch: %d problems, Omega ~ U{10..22}, seed 5" % len(probs),
+                      "total_dim": int(sum(dims)), "nnz_offdiag_per_batched_hx": int(nnz), "tol": args.tol,
+                      "window": args.window, "steps": args.steps, "l2": "flushed between steps",
+                      "mixed": out["mixed"], "fp64": out["fp64"],
+                      "speedup_mixed_vs_fp64": out["fp64"]["batch_ms"] / out["mixed"]["batch_ms"]}))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.batch:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

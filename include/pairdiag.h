@@ -185,6 +185,43 @@ int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec
  */
 int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ);
 
+/* ------------------------------------------------------------- batch ---- */
+
+typedef struct {
+    int    iterations;      /* Lanczos H*x products of this problem */
+    int    converged;       /* 1 if its residual reached tol */
+    int    stalled;         /* mixed form: FP32 cycles stopped at their rounding floor */
+    double rel_residual;    /* relative residual of the returned energy's vector: FP64
+                               ||Hv - Ev||/|E| after refinement (mixed), else |beta_1/alpha_1| */
+    double latency_ms;      /* device time from the start of the cycles to the end of the
+                               cycle in which this problem finished */
+} pairdiag_batch_result;
+
+/*
+ * Ground states of `count` independent pairing Hamiltonians (Eq. 2) in one
+ * lock-step restarted-Lanczos run: the mean-field use case of Sec. 1/6, where a
+ * pairing solve sits inside every self-consistent iteration.  Every kernel
+ * serves all problems in one launch; converged problems drop out; each restart
+ * cycle is replayed from a captured CUDA graph.
+ *   omega, n_pairs : host [count]
+ *   e_all          : host, the e vectors of all problems concatenated (sum of omega)
+ *   G_all          : host, the row-major G matrices concatenated (sum of omega^2);
+ *                    each exactly symmetric
+ *   tol            : |beta_1/alpha_1| (Sec. 5.1); the mixed form refines every
+ *                    vector in FP64 and reports that residual instead
+ *   opt            : nullable; window, max_restarts, precision, seed, low_bits and
+ *                    mixed_floor are used; start must be PD_START_RANDOM, mode 0
+ *   e0, status     : host [count] outputs (PD_OK or PD_ENOCONV per problem)
+ *   results        : host [count], nullable
+ *   stream         : cudaStream_t as void* (nullptr = legacy default stream)
+ * Device memory is allocated for the call and freed before it returns.
+ * Returns PD_OK, PD_ENOCONV if any problem missed tol (all outputs filled), or
+ * another PD_E* code.  Synchronous.
+ */
+int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs, const double *e_all,
+                                const double *G_all, double tol, const pairdiag_options *opt,
+                                double *e0, int *status, pairdiag_batch_result *results, void *stream);
+
 /* ------------------------------------------------------- diagnostics ---- */
 
 /* Number of CUDA kernels this library has launched since it was loaded (all

@@ -26,8 +26,10 @@ std::atomic<long long> g_kernel_launches{0};
 }
 
 namespace {
-
 thread_local std::string g_last_error = "no error";
+}
+
+namespace pd {
 
 int fail(int code, const char *fmt, ...)
 {
@@ -39,20 +41,6 @@ int fail(int code, const char *fmt, ...)
     g_last_error = buf;
     return code;
 }
-
-#define PD_CUDA(call)                                                                   \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return fail(e_ == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA,         \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
-
-#define PD_TRY(call)                \
-    do {                            \
-        int s_ = (call);            \
-        if (s_ != PD_OK) return s_; \
-    } while (0)
 
 uint64_t host_binom(int n, int m)
 {
@@ -70,7 +58,32 @@ uint64_t host_binom(int n, int m)
     return table[n][m];
 }
 
-}  // namespace
+// words of `bits` bits with `c` set bits, ascending (Gosper's successor)
+void words_with_popcount(int bits, int c, std::vector<uint64_t> &out)
+{
+    if (c == 0) { out.push_back(0); return; }
+    if (c > bits) return;
+    uint64_t w = (c == 64) ? ~0ull : ((1ull << c) - 1ull);
+    const uint64_t last = w << (bits - c);
+    for (;;) {
+        out.push_back(w);
+        if (w == last) break;
+        const uint64_t lowest = w & (~w + 1ull);
+        const uint64_t ripple = w + lowest;
+        w = ripple | (((w ^ ripple) >> 2) / lowest);
+    }
+}
+
+uint64_t host_block_base(uint64_t hw, int L, int N)
+{
+    int ord = N - __builtin_popcountll(hw);
+    uint64_t s = 0;
+    for (int p = 0; p < 64; ++p)
+        if (hw >> p & 1ull) s += host_binom(L + p, ++ord);
+    return s;
+}
+
+}  // namespace pd
 
 struct pairdiag {
     int omega = 0, n = 0;
@@ -141,31 +154,6 @@ int upload(T **p, const std::vector<T> &v)
     PD_TRY(dalloc(p, v.size()));
     PD_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     return PD_OK;
-}
-
-// words of `bits` bits with `c` set bits, ascending (Gosper's successor)
-void words_with_popcount(int bits, int c, std::vector<uint64_t> &out)
-{
-    if (c == 0) { out.push_back(0); return; }
-    if (c > bits) return;
-    uint64_t w = (c == 64) ? ~0ull : ((1ull << c) - 1ull);
-    const uint64_t last = w << (bits - c);
-    for (;;) {
-        out.push_back(w);
-        if (w == last) break;
-        const uint64_t lowest = w & (~w + 1ull);
-        const uint64_t ripple = w + lowest;
-        w = ripple | (((w ^ ripple) >> 2) / lowest);
-    }
-}
-
-uint64_t host_block_base(uint64_t hw, int L, int N)
-{
-    int ord = N - __builtin_popcountll(hw);
-    uint64_t s = 0;
-    for (int p = 0; p < 64; ++p)
-        if (hw >> p & 1ull) s += host_binom(L + p, ++ord);
-    return s;
 }
 
 int build_tables(pairdiag *h)

@@ -79,6 +79,151 @@ __device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
     return s;
 }
 
+// One basis block (high word h, first index base) of y = H x.  x and y point at
+// the problem's own vector; sG/sd/sRank hold its G, d and rank table.  Called
+// by every thread of the CTA (it contains barriers).
+template <typename T, typename A, int R>
+__device__ __forceinline__ void hx_block(const int omega, const int L, const int H, const int N,
+                                         const uint64_t h, const uint64_t base,
+                                         const uint16_t *__restrict__ lowword,
+                                         const uint64_t *__restrict__ binom,
+                                         const A *sG, const A *sd, const uint16_t *sRank, T *sx, T *sxn,
+                                         HHop<A> *sHH, uint64_t *sMX, const T *__restrict__ x,
+                                         T *__restrict__ y)
+{
+    const int tid = threadIdx.x;
+    const uint32_t maskL = (1u << L) - 1u;
+    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
+    const int ph = __popcll(h);
+    const int k = N - ph;                     // pairs in the low orbits
+    const int nk = (int)__ldg(binom + L * kBinomStride + k);
+    int lo_off_k = 0;
+    for (int j = 0; j < k; ++j) lo_off_k += (int)__ldg(binom + L * kBinomStride + j);
+    const uint16_t *lw = lowword + lo_off_k;
+    const int nemp = H - ph;
+    const int nhh = ph * nemp;
+
+    // CTA-uniform hop tables of this block
+    for (int t = tid; t < nhh; t += kThreads) {
+        const int a = t / nemp, c = t - a * nemp;
+        const int o = nth_set_bit(h, a);
+        const int q = nth_set_bit(~h & maskH, c);
+        sHH[t].base = block_base(h ^ (1ull << o) ^ (1ull << q), L, N, binom);
+        sHH[t].g = sG[(L + q) * omega + (L + o)];
+    }
+    for (int t = tid; t < H; t += kThreads) {
+        const uint64_t bit = 1ull << t;
+        const bool occ = (h & bit) != 0;
+        const bool ok = occ ? (k + 1 <= L) : (k >= 1);
+        sMX[t] = ok ? block_base(h ^ bit, L, N, binom) : ~0ull;
+    }
+    for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
+    __syncthreads();
+
+    A Dh = A(0);
+    for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
+
+    uint32_t lr[R];
+    A acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        lr[i] = 0;
+        acc[i] = A(0);
+        if (r < nk) {
+            const uint32_t l = lw[r];
+            lr[i] = l;
+            A D = A(0);
+            for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
+            acc[i] = (D + Dh) * A(sx[r]);
+        }
+    }
+
+    // low -> low
+    if (k > 0 && k < L) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (tid + i * kThreads < nk) {
+                const uint32_t l = lr[i];
+                A a = acc[i];
+                uint32_t occ = l;
+                for (int u = 0; u < k; ++u) {
+                    const int o = __ffs(occ) - 1;
+                    occ &= occ - 1;
+                    const uint32_t lo = l ^ (1u << o);
+                    uint32_t emp = ~l & maskL;
+                    for (int v = 0; v < L - k; ++v) {
+                        const int q = __ffs(emp) - 1;
+                        emp &= emp - 1;
+                        a += sG[q * omega + o] * A(sx[sRank[lo | (1u << q)]]);
+                    }
+                }
+                acc[i] = a;
+            }
+        }
+    }
+
+    // high -> high: same offsets in the target block
+    for (int j = 0; j < nhh; ++j) {
+        const T *xb = x + sHH[j].base;
+        const A g = sHH[j].g;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) acc[i] += g * A(__ldg(xb + r));
+        }
+    }
+
+    // high <-> low: stage each neighbouring block once
+    for (int t = 0; t < H; ++t) {
+        const uint64_t b2 = sMX[t];
+        if (b2 == ~0ull) continue;            // CTA-uniform
+        const bool occ_t = (h >> t) & 1ull;
+        const int n2 = (int)__ldg(binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
+        __syncthreads();
+        for (int r = tid; r < n2; r += kThreads) sxn[r] = x[b2 + r];
+        __syncthreads();
+        const int go = L + t;
+        if (occ_t) {                           // pair: high orbit go -> empty low orbit q
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (tid + i * kThreads < nk) {
+                    const uint32_t l = lr[i];
+                    A a = acc[i];
+                    uint32_t emp = ~l & maskL;
+                    for (int v = 0; v < L - k; ++v) {
+                        const int q = __ffs(emp) - 1;
+                        emp &= emp - 1;
+                        a += sG[q * omega + go] * A(sxn[sRank[l | (1u << q)]]);
+                    }
+                    acc[i] = a;
+                }
+            }
+        } else {                               // pair: occupied low orbit o -> high orbit go
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (tid + i * kThreads < nk) {
+                    const uint32_t l = lr[i];
+                    A a = acc[i];
+                    uint32_t occ = l;
+                    for (int u = 0; u < k; ++u) {
+                        const int o = __ffs(occ) - 1;
+                        occ &= occ - 1;
+                        a += sG[go * omega + o] * A(sxn[sRank[l ^ (1u << o)]]);
+                    }
+                    acc[i] = a;
+                }
+            }
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        if (r < nk) y[base + r] = T(acc[i]);
+    }
+}
+
 template <typename T, typename A, int R>
 __global__ void __launch_bounds__(kThreads)
 hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
@@ -102,8 +247,6 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     for (int i = tid; i < omega * omega; i += kThreads) sG[i] = Gg[i];
     for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
     for (int i = tid; i < (1 << L); i += kThreads) sRank[i] = B.rankL[i];
-    const uint32_t maskL = (1u << L) - 1u;
-    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
 
     for (;;) {
         __syncthreads();                          // smem of the previous block is free
@@ -112,134 +255,58 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
         const long long b = s_next;
         if (b >= B.nblocks) break;
 
-        const uint64_t h = __ldg(B.blk_h + b);
-        const uint64_t base = __ldg(B.blk_base + b);
-        const int ph = __popcll(h);
-        const int k = N - ph;                     // pairs in the low orbits
-        const int nk = (int)__ldg(B.binom + L * kBinomStride + k);
-        const uint16_t *lw = B.lowword + B.lo_off[k];
-        const int nemp = H - ph;
-        const int nhh = ph * nemp;
+        hx_block<T, A, R>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
+                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y);
+    }
+}
 
-        // CTA-uniform hop tables of this block
-        for (int t = tid; t < nhh; t += kThreads) {
-            const int a = t / nemp, c = t - a * nemp;
-            const int o = nth_set_bit(h, a);
-            const int q = nth_set_bit(~h & maskH, c);
-            sHH[t].base = block_base(h ^ (1ull << o) ^ (1ull << q), L, N, B.binom);
-            sHH[t].g = sG[(L + q) * omega + (L + o)];
-        }
-        for (int t = tid; t < H; t += kThreads) {
-            const uint64_t bit = 1ull << t;
-            const bool occ = (h & bit) != 0;
-            const bool ok = occ ? (k + 1 <= L) : (k >= 1);
-            sMX[t] = ok ? block_base(h ^ bit, L, N, B.binom) : ~0ull;
-        }
-        for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
+// ---- batched: blocks of many problems in one launch ----------------------------
+// The global block list is sorted by problem.  A CTA reloads the problem's G, d
+// and rank table only when the next block it takes belongs to another problem;
+// problems flagged in skip[] (converged, or broken down in this cycle) are
+// passed over.
+template <typename T, typename A, int R>
+__global__ void __launch_bounds__(kThreads)
+hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__restrict__ dall,
+                const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
+                const int *__restrict__ skip, int skip_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_next;
+    const Layout lay = layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh);
+    A *sG = reinterpret_cast<A *>(smem + lay.G);
+    A *sd = reinterpret_cast<A *>(smem + lay.d);
+    uint16_t *sRank = reinterpret_cast<uint16_t *>(smem + lay.rank);
+    T *sx = reinterpret_cast<T *>(smem + lay.x);
+    T *sxn = reinterpret_cast<T *>(smem + lay.xn);
+    HHop<A> *sHH = reinterpret_cast<HHop<A> *>(smem + lay.hh);
+    uint64_t *sMX = reinterpret_cast<uint64_t *>(smem + lay.mx);
+    const int tid = threadIdx.x;
+    int cur = -1;
+    BatchDesc dsc{};
+
+    for (;;) {
+        __syncthreads();                          // smem of the previous block is free
+        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
-
-        A Dh = A(0);
-        for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
-
-        uint32_t lr[R];
-        A acc[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int r = tid + i * kThreads;
-            lr[i] = 0;
-            acc[i] = A(0);
-            if (r < nk) {
-                const uint32_t l = lw[r];
-                lr[i] = l;
-                A D = A(0);
-                for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
-                acc[i] = (D + Dh) * A(sx[r]);
-            }
-        }
-
-        // low -> low
-        if (k > 0 && k < L) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                if (tid + i * kThreads < nk) {
-                    const uint32_t l = lr[i];
-                    A a = acc[i];
-                    uint32_t occ = l;
-                    for (int u = 0; u < k; ++u) {
-                        const int o = __ffs(occ) - 1;
-                        occ &= occ - 1;
-                        const uint32_t lo = l ^ (1u << o);
-                        uint32_t emp = ~l & maskL;
-                        for (int v = 0; v < L - k; ++v) {
-                            const int q = __ffs(emp) - 1;
-                            emp &= emp - 1;
-                            a += sG[q * omega + o] * A(sx[sRank[lo | (1u << q)]]);
-                        }
-                    }
-                    acc[i] = a;
-                }
-            }
-        }
-
-        // high -> high: same offsets in the target block
-        for (int j = 0; j < nhh; ++j) {
-            const T *xb = x + sHH[j].base;
-            const A g = sHH[j].g;
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = tid + i * kThreads;
-                if (r < nk) acc[i] += g * A(__ldg(xb + r));
-            }
-        }
-
-        // high <-> low: stage each neighbouring block once
-        for (int t = 0; t < H; ++t) {
-            const uint64_t b2 = sMX[t];
-            if (b2 == ~0ull) continue;            // CTA-uniform
-            const bool occ_t = (h >> t) & 1ull;
-            const int n2 = (int)__ldg(B.binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
+        const long long b = s_next;
+        if (b >= BB.nblocks) break;
+        const int pb = (int)__ldg(BB.blk_prob + b);
+        if (skip && skip[(int64_t)pb * skip_stride]) continue;   // CTA-uniform
+        if (pb != cur) {
+            dsc = BB.desc[pb];
+            const A *G = Gall + dsc.g_off;
+            const A *d = dall + dsc.d_off;
+            for (int i = tid; i < dsc.omega * dsc.omega; i += kThreads) sG[i] = G[i];
+            for (int i = tid; i < dsc.omega; i += kThreads) sd[i] = d[i];
+            const uint16_t *rk = BB.rankL_all + dsc.tab_off;
+            for (int i = tid; i < (1 << dsc.L); i += kThreads) sRank[i] = rk[i];
+            cur = pb;
             __syncthreads();
-            for (int r = tid; r < n2; r += kThreads) sxn[r] = x[b2 + r];
-            __syncthreads();
-            const int go = L + t;
-            if (occ_t) {                           // pair: high orbit go -> empty low orbit q
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    if (tid + i * kThreads < nk) {
-                        const uint32_t l = lr[i];
-                        A a = acc[i];
-                        uint32_t emp = ~l & maskL;
-                        for (int v = 0; v < L - k; ++v) {
-                            const int q = __ffs(emp) - 1;
-                            emp &= emp - 1;
-                            a += sG[q * omega + go] * A(sxn[sRank[l | (1u << q)]]);
-                        }
-                        acc[i] = a;
-                    }
-                }
-            } else {                               // pair: occupied low orbit o -> high orbit go
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    if (tid + i * kThreads < nk) {
-                        const uint32_t l = lr[i];
-                        A a = acc[i];
-                        uint32_t occ = l;
-                        for (int u = 0; u < k; ++u) {
-                            const int o = __ffs(occ) - 1;
-                            occ &= occ - 1;
-                            a += sG[go * omega + o] * A(sxn[sRank[l ^ (1u << o)]]);
-                        }
-                        acc[i] = a;
-                    }
-                }
-            }
         }
-
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int r = tid + i * kThreads;
-            if (r < nk) y[base + r] = T(acc[i]);
-        }
+        hx_block<T, A, R>(dsc.omega, dsc.L, dsc.omega - dsc.L, dsc.n, __ldg(BB.blk_h + b), __ldg(BB.blk_base + b),
+                          BB.lowword_all + dsc.tab_off, BB.binom, sG, sd, sRank, sx, sxn, sHH, sMX,
+                          x + dsc.vec_off, y + dsc.vec_off);
     }
 }
 
@@ -669,6 +736,69 @@ cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const 
     auto *ctr = reinterpret_cast<unsigned long long *>(counter);
     if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, ctr, grid, st, skip);
     return launch_prec<float, float>(B, P.G32, P.d32, x, y, ctr, grid, st, skip);
+}
+
+namespace {
+template <typename T, typename A, int R>
+const void *batch_fn() { return (const void *)hx_batch_kernel<T, A, R>; }
+
+template <typename T, typename A>
+const void *batch_fn_rows(int rows)
+{
+    return rows <= 1 ? batch_fn<T, A, 1>() : rows <= 2 ? batch_fn<T, A, 2>() : rows <= 4 ? batch_fn<T, A, 4>()
+                                                                                          : batch_fn<T, A, 8>();
+}
+
+template <typename T, typename A>
+cudaError_t batch_launch_t(const BatchBlocks &BB, const A *G, const A *d, const void *x, void *y,
+                           unsigned long long *counter, int grid, cudaStream_t st, const int *skip,
+                           int skip_stride)
+{
+    const size_t smem = layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh).total;
+    const int rows = (BB.max_block + kThreads - 1) / kThreads;
+    cudaError_t err = cudaFuncSetAttribute(batch_fn_rows<T, A>(rows),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return err;
+    const T *xt = static_cast<const T *>(x);
+    T *yt = static_cast<T *>(y);
+    if (rows <= 1) hx_batch_kernel<T, A, 1><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+    else if (rows <= 2) hx_batch_kernel<T, A, 2><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+    else if (rows <= 4) hx_batch_kernel<T, A, 4><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+    else hx_batch_kernel<T, A, 8><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, typename A>
+int batch_grid_t(const BatchBlocks &BB)
+{
+    const size_t smem = layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh).total;
+    const void *fn = batch_fn_rows<T, A>((BB.max_block + kThreads - 1) / kThreads);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > BB.nblocks) g = BB.nblocks;
+    return (int)(g > 0 ? g : 1);
+}
+}  // namespace
+
+cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
+                            int *counter, int grid, cudaStream_t st, const int *skip, int skip_stride)
+{
+    auto *ctr = reinterpret_cast<unsigned long long *>(counter);
+    if (precision == 0) return batch_launch_t<double, double>(BB, P.G64, P.d64, x, y, ctr, grid, st, skip, skip_stride);
+    return batch_launch_t<float, float>(BB, P.G32, P.d32, x, y, ctr, grid, st, skip, skip_stride);
+}
+
+int hx_batch_grid(const BatchBlocks &BB, int precision)
+{
+    return precision == 0 ? batch_grid_t<double, double>(BB) : batch_grid_t<float, float>(BB);
 }
 
 cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,

@@ -13,9 +13,31 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace pd {
+
+// ---- host helpers (pd_api.cu) ------------------------------------------------
+// record a one-line error for pairdiag_last_error() and return `code`
+int fail(int code, const char *fmt, ...);
+uint64_t host_binom(int n, int m);                        // Pascal table, 0 outside 0 <= m <= n <= 63
+uint64_t host_block_base(uint64_t hw, int L, int N);      // index of the block with high word hw
+void words_with_popcount(int bits, int c, std::vector<uint64_t> &out);   // ascending
+
+#define PD_CUDA(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return ::pd::fail(e_ == cudaErrorMemoryAllocation ? -2 : -5, "%s: %s (%s:%d)", #call, \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+#define PD_TRY(call)                \
+    do {                            \
+        int s_ = (call);            \
+        if (s_ != 0) return s_;     \
+    } while (0)
 
 // kernels launched by the library (diagnostic counter, defined in pd_api.cu)
 extern std::atomic<long long> g_kernel_launches;
@@ -40,6 +62,27 @@ struct Blocks {
     int variant;                     // H*x kernel: 0 automatic, 1 staged per neighbour, 2 all staged
 };
 
+// ---- many problems at once (batched solver) ---------------------------------
+struct BatchDesc {                   // one problem of a batch (device array)
+    int omega, n, L;                 // H = omega - L
+    int g_off;                       // offset of its G in the concatenated G arrays
+    int d_off;                       // offset of its d in the concatenated d arrays
+    int tab_off;                     // offset of its L's tables in lowword_all / rankL_all
+    int64_t vec_off;                 // offset of its first element in concatenated vectors
+    int64_t dim;
+};
+struct BatchBlocks {
+    int64_t nblocks;                 // all problems
+    const uint32_t *blk_prob;        // [nblocks] owning problem, non-decreasing
+    const uint64_t *blk_h;           // [nblocks] high word
+    const uint64_t *blk_base;        // [nblocks] index of the block's first state within its problem
+    const BatchDesc *desc;           // [count]
+    const uint16_t *lowword_all;     // per-L tables, concatenated
+    const uint16_t *rankL_all;
+    const uint64_t *binom;
+    int max_omega, max_L, max_H, max_block, max_hh;   // bounds for the shared-memory layout
+};
+
 // ---- H*x (pd_hx.cu) -------------------------------------------------------
 // precision 0: double vectors / double accumulation with G64, d64
 // precision 1: float vectors / float accumulation with G32, d32
@@ -47,6 +90,10 @@ struct HxProblem {
     const double *G64, *d64;         // G [omega*omega], d_p = 2 e_p + G_pp
     const float *G32, *d32;
 };
+// batched H*x: skip[p * skip_stride] != 0 passes over problem p (skip nullable)
+cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
+                            int *counter, int grid, cudaStream_t st, const int *skip, int skip_stride);
+int hx_batch_grid(const BatchBlocks &BB, int precision);
 size_t hx_smem_bytes(const Blocks &B, int precision);
 int hx_variant(const Blocks &B, int precision);   // kernel variant a launch will use (1 or 2)
 // skip (nullable, device): when *skip != 0 the launched kernels return at once
@@ -113,5 +160,65 @@ cudaError_t convert_launch(int dst_dtype, void *dst, int src_dtype, const void *
 // dst = a - lambda * b (double), ||dst||^2 -> *norm_out; lambda read from device
 cudaError_t residual_launch(const double *a, const double *b, const double *lambda, double *dst,
                             int64_t n, double *partials, double *norm_out, cudaStream_t st);
+
+// ---- batched Lanczos (pd_lanczos.cu kernels, pd_batch.cu driver) -------------
+struct BatchState {                  // one problem (device memory)
+    double alpha[kMaxWindow];
+    double beta[kMaxWindow];
+    double c2[kMaxWindow];           // projections; also refinement scratch
+    double s[kMaxWindow];            // ground Ritz vector of the cycle's L matrix
+    double c1;                       // alpha from the three-term recurrence
+    double norm2, tnorm;
+    double theta[2];
+    double e0, rel;                  // energy estimate and |beta_1/alpha_1| (or FP64 residual)
+    double hist[4];                  // last restart residuals (stagnation test)
+    int used, broken, done, skip;    // skip = done || broken (kernels pass over the problem)
+    int iters, done_cycle, stalled, pad;
+};
+struct BatchVec {                    // vectors concatenated over problems, cut into chunks
+    int count;
+    int nchunks;                     // every chunk lies inside one problem; <= 32 per problem
+    int64_t total;
+    const int *chunk_prob;
+    const int64_t *chunk_start;      // global element index
+    const int *chunk_len;
+    const int *prob_chunk0;          // [count] first chunk of each problem
+    const int *prob_nchunk;          // [count]
+    const int64_t *prob_off;         // [count] first element of each problem
+};
+constexpr int kMaxChunksPerProblem = 32;
+
+// out[p * out_stride + j] = sum over problem p's elements of Q_j[e] v[e], j < m
+// (Q vector-major with leading dimension ldq); skipped problems are left alone
+cudaError_t seg_dots_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, const void *v,
+                            const int *skip, double *partials, double *out, int out_stride, cudaStream_t st);
+// per problem: v <- v - c1 q_i - beta[i-1] q_{i-1}; then c2[j] = Q_j^T v, j <= i
+cudaError_t seg_recur_project_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int i, void *v,
+                                     BatchState *S, double *partials, cudaStream_t st);
+// per problem: v <- v - sum_{j<m} c2[j] Q_j, norm2 = ||v||^2
+cudaError_t seg_update_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, void *v,
+                              BatchState *S, double *partials, cudaStream_t st);
+// dst <- src / beta[i] (mode 0) or src / sqrt(norm2) (mode 1), per problem
+cudaError_t seg_scale_launch(int dtype, const BatchVec &V, const void *src, void *dst, BatchState *S, int i,
+                             int mode, cudaStream_t st);
+// Q_0 <- sum_{j<used} s[j] Q_j per problem, norm2 = ||Q_0||^2
+cudaError_t seg_ritz_launch(int dtype, const BatchVec &V, void *Q, int64_t ldq, BatchState *S, double *partials,
+                            cudaStream_t st);
+cudaError_t seg_random_launch(int dtype, const BatchVec &V, void *q, uint64_t seed, cudaStream_t st);
+// per problem: residual r = w - e0 v (FP64), norm2 = ||r||^2
+cudaError_t seg_residual_launch(const BatchVec &V, const double *w, const double *v, BatchState *S,
+                                double *partials, cudaStream_t st);
+cudaError_t batch_reset_launch(BatchState *S, int count, cudaStream_t st);
+cudaError_t batch_finalize_launch(BatchState *S, int count, int i, cudaStream_t st);
+// after step 0 of a cycle: convergence / stagnation per problem; *active = problems still running
+cudaError_t batch_converge_launch(BatchState *S, int count, double tol, int cycle, int stall_check,
+                                  int *active, cudaStream_t st);
+cudaError_t batch_tridiag_launch(BatchState *S, int count, cudaStream_t st);
+// after refinement: problems with rel > tol reopen (done = skip = 0), the others are
+// finished; *reopened = number reopened
+cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, int last_cycle, int *reopened,
+                                cudaStream_t st);
+// e0 = c2[0] / c2[1] (Rayleigh quotient from v^T w and v^T v)
+cudaError_t batch_rayleigh_launch(BatchState *S, int count, int stage, cudaStream_t st);
 
 }  // namespace pd

@@ -353,21 +353,22 @@ __device__ void tridiag_solve(const double *a, const double *b, int m, double th
     }
 }
 
-__global__ void tridiag_kernel(LanczosScalars *S, int m)
+// Lowest two eigenvalues and the lowest eigenvector of the m x m symmetric
+// tridiagonal matrix (alpha, beta), computed by one warp.  The work arrays live
+// in shared memory (kMaxWindow doubles each).
+__device__ void tridiag_warp(const double *alpha, const double *beta, int m, double *theta_out, double *s_out,
+                             double *a, double *b, double *b2, double *z, double *u0, double *u1, double *u2)
 {
-    __shared__ double a[kMaxWindow], b[kMaxWindow], b2[kMaxWindow];
-    __shared__ double z[kMaxWindow], u0[kMaxWindow], u1[kMaxWindow], u2[kMaxWindow];
-    const int lane = threadIdx.x;
-    if (m <= 0) m = S->used;
-    if (m < 1 || m > kMaxWindow) return;
+    const int lane = threadIdx.x & 31;
     for (int i = lane; i < m; i += 32) {
-        a[i] = S->alpha[i];
-        b[i] = (i + 1 < m) ? S->beta[i] : 0.0;
+        a[i] = alpha[i];
+        b[i] = (i + 1 < m) ? beta[i] : 0.0;
         b2[i] = b[i] * b[i];
     }
     __syncwarp();
     if (m == 1) {
-        if (lane == 0) { S->theta[0] = a[0]; S->theta[1] = INFINITY; S->s[0] = 1.0; }
+        if (lane == 0) { theta_out[0] = a[0]; theta_out[1] = INFINITY; s_out[0] = 1.0; }
+        __syncwarp();
         return;
     }
     // Gershgorin interval and the scale of T
@@ -395,10 +396,20 @@ __global__ void tridiag_kernel(LanczosScalars *S, int m)
         double big = 0.0; int ib = 0;                 // fix the sign: largest component positive
         for (int i = 0; i < m; ++i) if (fabs(z[i]) > big) { big = fabs(z[i]); ib = i; }
         const double sg = z[ib] < 0.0 ? -1.0 : 1.0;
-        for (int i = 0; i < m; ++i) S->s[i] = sg * z[i];
-        S->theta[0] = t1;
-        S->theta[1] = t2;
+        for (int i = 0; i < m; ++i) s_out[i] = sg * z[i];
+        theta_out[0] = t1;
+        theta_out[1] = t2;
     }
+    __syncwarp();
+}
+
+__global__ void tridiag_kernel(LanczosScalars *S, int m)
+{
+    __shared__ double a[kMaxWindow], b[kMaxWindow], b2[kMaxWindow];
+    __shared__ double z[kMaxWindow], u0[kMaxWindow], u1[kMaxWindow], u2[kMaxWindow];
+    if (m <= 0) m = S->used;
+    if (m < 1 || m > kMaxWindow) return;
+    tridiag_warp(S->alpha, S->beta, m, S->theta, S->s, a, b, b2, z, u0, u1, u2);
 }
 
 // Q0 <- sum_j s_j Q_j (in place; each element is read before it is written)
@@ -488,6 +499,328 @@ residual_kernel(const double *__restrict__ a, const double *__restrict__ b,
     }
     const double s = block_sum(nrm, sh);
     if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
+}
+
+// ---- batched (segmented) kernels: vectors concatenated over problems ---------
+template <typename T>
+struct DotAcc {                       // FP64 products and sums
+    double v = 0.0;
+    __device__ __forceinline__ void add(T a, T b) { v = fma((double)a, (double)b, v); }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct DotAcc<float> {                // float-float (exact products, TwoSum)
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(hi, lo, a, b); }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ v,
+                const BatchState *__restrict__ S, int use_skip, double *__restrict__ part)
+{
+    __shared__ double sh[kThreads / 32];
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        if (use_skip && S[pr].skip) continue;                // CTA-uniform
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        for (int j0 = 0; j0 < m; j0 += kGroup) {
+            DotAcc<T> acc[kGroup];
+            for (int e = threadIdx.x; e < len; e += kThreads) {
+                const T pv = v[e0 + e];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) acc[u].add(__ldg(Q + (int64_t)(j0 + u) * ldq + e0 + e), pv);
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                if (j0 + u < m) {
+                    const double sum = block_sum(acc[u].get(), sh);
+                    if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
+                }
+            }
+        }
+    }
+}
+
+// one warp per (problem, output): lane l adds chunk l of the problem (<= 32 chunks).
+// use_skip: 0 every problem, 1 pass over problems with skip set, 2 pass over done ones
+__global__ void seg_reduce_kernel(const BatchVec V, int m, const BatchState *__restrict__ S, int use_skip,
+                                  const double *__restrict__ part, double *__restrict__ out, int out_stride)
+{
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int pr = w / m, j = w - pr * m;
+    if (pr >= V.count) return;
+    if ((use_skip == 1 && S[pr].skip) || (use_skip == 2 && S[pr].done)) return;   // warp-uniform
+    const int nc = V.prob_nchunk[pr], c0 = V.prob_chunk0[pr];
+    double sum = lane < nc ? part[(int64_t)(c0 + lane) * kMaxWindow + j] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) out[(int64_t)pr * out_stride + j] = sum;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int i, T *__restrict__ v,
+                         const BatchState *__restrict__ S, double *__restrict__ part)
+{
+    __shared__ double sh[kThreads / 32];
+    const int m = i + 1;
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        if (S[pr].skip) continue;
+        const T a = (T)S[pr].c1;
+        const T b = (T)(i > 0 ? S[pr].beta[i - 1] : 0.0);
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        const T *qi = Q + (int64_t)i * ldq + e0;
+        const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq + e0;
+        for (int j0 = 0; j0 < m; j0 += kGroup) {
+            DotAcc<T> acc[kGroup];
+            for (int e = threadIdx.x; e < len; e += kThreads) {
+                T x = v[e0 + e];
+                if (j0 == 0) {                                  // same thread, same element in later groups
+                    x = fma_t<T>(-a, __ldg(qi + e), x);
+                    if (i > 0) x = fma_t<T>(-b, __ldg(qm + e), x);
+                    v[e0 + e] = x;
+                }
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) acc[u].add(__ldg(Q + (int64_t)(j0 + u) * ldq + e0 + e), x);
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                if (j0 + u < m) {
+                    const double sum = block_sum(acc[u].get(), sh);
+                    if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+seg_update_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, T *__restrict__ v,
+                  const BatchState *__restrict__ S, double *__restrict__ part)
+{
+    __shared__ T sc[kMaxWindow];
+    __shared__ double sh[kThreads / 32];
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        if (S[pr].skip) continue;
+        __syncthreads();                                        // sc of the previous chunk consumed
+        for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = (T)S[pr].c2[j];
+        __syncthreads();
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        DotAcc<T> nrm;
+        for (int e = threadIdx.x; e < len; e += kThreads) {
+            T x = v[e0 + e];
+            for (int j = 0; j < m; ++j) x = fma_t<T>(-sc[j], __ldg(Q + (int64_t)j * ldq + e0 + e), x);
+            v[e0 + e] = x;
+            nrm.add(x, x);
+        }
+        const double sum = block_sum(nrm.get(), sh);
+        if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+seg_scale_kernel(const BatchVec V, const T *__restrict__ src, T *__restrict__ dst, const BatchState *__restrict__ S,
+                 int i, int mode)
+{
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        if (mode == 0 ? S[pr].skip : S[pr].done) continue;
+        const double d = mode == 0 ? S[pr].beta[i] : sqrt(S[pr].norm2);
+        const T f = (T)(d > 0.0 ? 1.0 / d : 0.0);
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        for (int e = threadIdx.x; e < len; e += kThreads) dst[e0 + e] = src[e0 + e] * f;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+seg_ritz_kernel(const BatchVec V, T *__restrict__ Q, int64_t ldq, const BatchState *__restrict__ S,
+                double *__restrict__ part)
+{
+    __shared__ T ss[kMaxWindow];
+    __shared__ double sh[kThreads / 32];
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        if (S[pr].done) continue;
+        const int m = S[pr].used;
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = (T)S[pr].s[j];
+        __syncthreads();
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        DotAcc<T> nrm;
+        for (int e = threadIdx.x; e < len; e += kThreads) {
+            T x = T(0);
+            for (int j = 0; j < m; ++j) x = fma_t<T>(ss[j], Q[(int64_t)j * ldq + e0 + e], x);
+            Q[e0 + e] = x;
+            nrm.add(x, x);
+        }
+        const double sum = block_sum(nrm.get(), sh);
+        if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+seg_residual_kernel(const BatchVec V, const double *__restrict__ w, const double *__restrict__ v,
+                    const BatchState *__restrict__ S, double *__restrict__ part)
+{
+    __shared__ double sh[kThreads / 32];
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        const double lam = S[pr].e0;
+        const int64_t e0 = V.chunk_start[c];
+        const int len = V.chunk_len[c];
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < len; e += kThreads) {
+            const double r = w[e0 + e] - lam * v[e0 + e];
+            acc = fma(r, r, acc);
+        }
+        const double sum = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
+    }
+}
+
+template <typename T>
+__global__ void seg_random_kernel(const BatchVec V, T *__restrict__ q, uint64_t seed)
+{
+    for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
+        const int pr = V.chunk_prob[c];
+        const int64_t e0 = V.chunk_start[c];
+        const int64_t local0 = e0 - V.prob_off[pr];
+        const int len = V.chunk_len[c];
+        for (int e = threadIdx.x; e < len; e += blockDim.x)
+            q[e0 + e] = (T)splitmix_uniform(seed, (uint64_t)(local0 + e));
+    }
+}
+
+__global__ void batch_reset_kernel(BatchState *S, int count)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= count) return;
+    S[pr].used = 0;
+    S[pr].broken = 0;
+    S[pr].tnorm = 0.0;
+    S[pr].skip = S[pr].done;
+}
+
+__global__ void batch_finalize_kernel(BatchState *S, int count, int i)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (P.skip) return;
+    const double a = P.c1 + P.c2[i];
+    const double b = sqrt(P.norm2);
+    P.alpha[i] = a;
+    P.beta[i] = b;
+    const double tn = fmax(P.tnorm, fabs(a) + b + (i > 0 ? P.beta[i - 1] : 0.0));
+    P.tnorm = tn;
+    P.used = i + 1;
+    P.iters += 1;
+    if (!(b > 1e-13 * tn)) { P.broken = 1; P.skip = 1; }
+}
+
+__global__ void batch_converge_kernel(BatchState *S, int count, double tol, int cycle, int stall_check,
+                                      int *active)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (P.done) return;
+    const double a = P.alpha[0], b = P.beta[0];
+    const double rel = (b == 0.0) ? 0.0 : b / fabs(a);
+    P.rel = rel;
+    P.e0 = a;
+    bool stop = rel <= tol;
+    if (!stop && stall_check) {
+        const double old = P.hist[0];
+        P.hist[0] = P.hist[1]; P.hist[1] = P.hist[2]; P.hist[2] = P.hist[3]; P.hist[3] = rel;
+        if (cycle >= 3 && rel > 0.7 * old) { stop = true; P.stalled = 1; }
+    }
+    if (stop) {
+        P.done = 1;
+        P.skip = 1;
+        P.done_cycle = cycle;
+    } else {
+        atomicAdd(active, 1);
+    }
+}
+
+__global__ void batch_tridiag_kernel(BatchState *S, int count)
+{
+    __shared__ double work[4][7][kMaxWindow];
+    const int wi = threadIdx.x >> 5;
+    const int pr = blockIdx.x * 4 + wi;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (P.done || P.used < 1) return;                        // warp-uniform
+    double (*w)[kMaxWindow] = work[wi];
+    tridiag_warp(P.alpha, P.beta, P.used, P.theta, P.s, w[0], w[1], w[2], w[3], w[4], w[5], w[6]);
+}
+
+// after the FP64 refinement: problems whose residual misses tol are reopened
+__global__ void batch_reopen_kernel(BatchState *S, int count, double tol, int last_cycle, int *reopened)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (P.rel <= tol) {                          // refined residual within tol: finished
+        if (!P.done) { P.done = 1; P.skip = 1; P.done_cycle = last_cycle; }
+        return;
+    }
+    P.done = 0;
+    P.skip = 0;
+    P.stalled = 0;
+    P.hist[0] = P.hist[1] = P.hist[2] = P.hist[3] = 0.0;
+    atomicAdd(reopened, 1);
+}
+
+__global__ void batch_rayleigh_kernel(BatchState *S, int count, int stage)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (stage == 0) {
+        P.e0 = P.c2[0] / P.c2[1];
+    } else {
+        const double r = sqrt(P.norm2 / P.c2[1]);
+        P.rel = (r == 0.0) ? 0.0 : r / fabs(P.e0);
+    }
+}
+
+int seg_grid(const BatchVec &V)
+{
+    int g = V.nchunks < 152 * 8 ? V.nchunks : 152 * 8;
+    return g > 0 ? g : 1;
+}
+
+inline int state_stride() { return (int)(sizeof(BatchState) / sizeof(double)); }
+
+inline void seg_reduce(const BatchVec &V, int m, const BatchState *S, int use_skip, const double *part,
+                       double *out, cudaStream_t st)
+{
+    const int64_t warps = (int64_t)V.count * m;
+    const int blocks = (int)((warps * 32 + 255) / 256);
+    seg_reduce_kernel<<<blocks, 256, 0, st>>>(V, m, S, use_skip, part, out, state_stride());
 }
 
 int grid_for(int64_t n)
@@ -620,6 +953,141 @@ cudaError_t residual_launch(const double *a, const double *b, const double *lamb
     residual_kernel<<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials);
     reduce(partials, g, 1, norm_out, st);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+// ---- batched launchers ---------------------------------------------------------
+cudaError_t seg_dots_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, const void *v,
+                            const int *skip, double *partials, double *out, int out_stride, cudaStream_t st)
+{
+    // skip != nullptr means: honour BatchState::skip (skip points at the state array)
+    const BatchState *S = reinterpret_cast<const BatchState *>(skip);
+    const int use_skip = skip != nullptr;
+    const int g = seg_grid(V);
+    if (dtype == 0)
+        seg_dots_kernel<double><<<g, kThreads, 0, st>>>(V, (const double *)Q, ldq, m, (const double *)v, S, use_skip, partials);
+    else
+        seg_dots_kernel<float><<<g, kThreads, 0, st>>>(V, (const float *)Q, ldq, m, (const float *)v, S, use_skip, partials);
+    const int64_t warps = (int64_t)V.count * m;
+    seg_reduce_kernel<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(V, m, S, use_skip, partials, out, out_stride);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_recur_project_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int i, void *v,
+                                     BatchState *S, double *partials, cudaStream_t st)
+{
+    const int g = seg_grid(V);
+    if (dtype == 0)
+        seg_recur_project_kernel<double><<<g, kThreads, 0, st>>>(V, (const double *)Q, ldq, i, (double *)v, S, partials);
+    else
+        seg_recur_project_kernel<float><<<g, kThreads, 0, st>>>(V, (const float *)Q, ldq, i, (float *)v, S, partials);
+    seg_reduce(V, i + 1, S, 1, partials, &S[0].c2[0], st);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_update_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, void *v,
+                              BatchState *S, double *partials, cudaStream_t st)
+{
+    const int g = seg_grid(V);
+    if (dtype == 0)
+        seg_update_kernel<double><<<g, kThreads, 0, st>>>(V, (const double *)Q, ldq, m, (double *)v, S, partials);
+    else
+        seg_update_kernel<float><<<g, kThreads, 0, st>>>(V, (const float *)Q, ldq, m, (float *)v, S, partials);
+    seg_reduce(V, 1, S, 1, partials, &S[0].norm2, st);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_scale_launch(int dtype, const BatchVec &V, const void *src, void *dst, BatchState *S, int i,
+                             int mode, cudaStream_t st)
+{
+    const int g = seg_grid(V);
+    if (dtype == 0)
+        seg_scale_kernel<double><<<g, kThreads, 0, st>>>(V, (const double *)src, (double *)dst, S, i, mode);
+    else
+        seg_scale_kernel<float><<<g, kThreads, 0, st>>>(V, (const float *)src, (float *)dst, S, i, mode);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_ritz_launch(int dtype, const BatchVec &V, void *Q, int64_t ldq, BatchState *S, double *partials,
+                            cudaStream_t st)
+{
+    const int g = seg_grid(V);
+    if (dtype == 0)
+        seg_ritz_kernel<double><<<g, kThreads, 0, st>>>(V, (double *)Q, ldq, S, partials);
+    else
+        seg_ritz_kernel<float><<<g, kThreads, 0, st>>>(V, (float *)Q, ldq, S, partials);
+    seg_reduce(V, 1, S, 2, partials, &S[0].norm2, st);      // problems still running
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_random_launch(int dtype, const BatchVec &V, void *q, uint64_t seed, cudaStream_t st)
+{
+    const int g = seg_grid(V);
+    if (dtype == 0) seg_random_kernel<double><<<g, kThreads, 0, st>>>(V, (double *)q, seed);
+    else seg_random_kernel<float><<<g, kThreads, 0, st>>>(V, (float *)q, seed);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_residual_launch(const BatchVec &V, const double *w, const double *v, BatchState *S,
+                                double *partials, cudaStream_t st)
+{
+    seg_residual_kernel<<<seg_grid(V), kThreads, 0, st>>>(V, w, v, S, partials);
+    seg_reduce(V, 1, S, 0, partials, &S[0].norm2, st);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_reset_launch(BatchState *S, int count, cudaStream_t st)
+{
+    batch_reset_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_finalize_launch(BatchState *S, int count, int i, cudaStream_t st)
+{
+    batch_finalize_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count, i);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_converge_launch(BatchState *S, int count, double tol, int cycle, int stall_check,
+                                  int *active, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(active, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    batch_converge_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count, tol, cycle, stall_check, active);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_tridiag_launch(BatchState *S, int count, cudaStream_t st)
+{
+    batch_tridiag_kernel<<<(count + 3) / 4, 128, 0, st>>>(S, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, int last_cycle, int *reopened,
+                                cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(reopened, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    batch_reopen_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count, tol, last_cycle, reopened);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_rayleigh_launch(BatchState *S, int count, int stage, cudaStream_t st)
+{
+    batch_rayleigh_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count, stage);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,11 @@ class pairdiag_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pairdiag_batch_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("stalled", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
 class PairDiagError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (status {code})")
@@ -70,6 +75,8 @@ _SIGNATURES = {
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
+    "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
+                                                   ctypes.POINTER(pairdiag_options), _P, _P, _P, _P]),
     "pairdiag_multidot_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P,
                                                  ctypes.c_int64, _P, _P]),
 }
@@ -245,6 +252,29 @@ def pairdiag_multidot_noalloc(Q, ld: int, m: int, p, n: int, out, stream=None) -
     sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().pairdiag_multidot_noalloc(dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n,
                                            _dev_ptr(out, torch.float64), ctypes.c_void_p(sp)))
+
+
+def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | None = None, stream=None) -> dict:
+    """problems: sequence of (omega, n_pairs, e, G).  Returns per-problem arrays
+    e0, status, iterations, converged, stalled, rel_residual, latency_ms and the
+    call's status."""
+    count = len(problems)
+    om = np.array([p[0] for p in problems], dtype=np.int32)
+    nn = np.array([p[1] for p in problems], dtype=np.int32)
+    e_all = np.ascontiguousarray(np.concatenate([np.asarray(p[2], dtype=np.float64).ravel() for p in problems]))
+    G_all = np.ascontiguousarray(np.concatenate([np.asarray(p[3], dtype=np.float64).ravel() for p in problems]))
+    e0 = np.empty(count)
+    status = np.empty(count, dtype=np.int32)
+    res = (pairdiag_batch_result * count)()
+    sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    st = _check(lib().pairdiag_batch_ground_state(count, _np_ptr(om), _np_ptr(nn), _np_ptr(e_all), _np_ptr(G_all),
+                                                  tol, ctypes.byref(opt) if opt is not None else None,
+                                                  _np_ptr(e0), _np_ptr(status), ctypes.cast(res, ctypes.c_void_p),
+                                                  ctypes.c_void_p(sp)), allow=(PD_OK, PD_ENOCONV))
+    out = dict(e0=e0, status=status, call_status=st)
+    for f, _ in pairdiag_batch_result._fields_:
+        out[f] = np.array([getattr(r, f) for r in res])
+    return out
 
 
 def pairdiag_tridiag_lowest(h, alpha, beta):

@@ -1,0 +1,76 @@
+"""Batched ground states (many Hamiltonians in one lock-step run) against
+single-problem solves and the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pd_inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+pd = pytest.importorskip("paper_2001_01978_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def small_batch():
+    probs = []
+    spec = [(6, 3), (7, 0), (8, 1), (9, 8), (10, 5), (11, 4), (12, 6), (13, 7), (14, 5), (15, 9), (16, 8), (17, 6)]
+    for i, (om, n) in enumerate(spec):
+        e, G = pd_inputs.separable_noise(om, seed=100 + i)
+        probs.append((om, n, e, G))
+    return probs
+
+
+@pytest.mark.parametrize("precision,rel", [(0, 1e-11), (1, 1e-8)])
+def test_small_batch_vs_oracle(precision, rel):
+    probs = small_batch()
+    opt = pd.pairdiag_default_options(precision=precision, window=20)
+    r = pd.pairdiag_batch_ground_state(probs, 1e-11 if precision == 0 else 1e-6, opt)
+    assert r["call_status"] == pd.PD_OK, r["status"]
+    for i, (om, n, e, G) in enumerate(probs):
+        ref = oracle.lanczos_ground(om, n, e, G, window=40, tol=1e-13)["e0"]
+        scale = max(1.0, abs(ref))
+        assert abs(r["e0"][i] - ref) <= rel * scale, (i, om, n, r["e0"][i], ref)
+        assert r["converged"][i] == 1
+    assert np.all(r["latency_ms"] > 0) or r["latency_ms"].max() > 0
+
+
+def test_batch_matches_single_solves_fp64():
+    probs = small_batch()
+    opt = pd.pairdiag_default_options(precision=pd.PD_PREC_FP64, window=20, seed=7)
+    r = pd.pairdiag_batch_ground_state(probs, 1e-12, opt)
+    for i, (om, n, e, G) in enumerate(probs):
+        with pd.Solver(om, n, e, G, window=20, seed=7) as s:
+            one = s.ground_state(1e-12, want_vector=False)
+        assert abs(r["e0"][i] - one["e0"]) <= 1e-11 * max(1.0, abs(one["e0"]))
+
+
+def test_workload_4096_stratified_subset():
+    """The 4096-problem mean-field workload (Omega ~ U{10..22}): mixed form in one
+    run; a stratified subset of problems against the oracle (small dims) and
+    single-problem FP64 solves (large dims)."""
+    probs = pd_inputs.batch_workload(4096, seed=5)
+    opt = pd.pairdiag_default_options(precision=pd.PD_PREC_MIXED, window=20)
+    r = pd.pairdiag_batch_ground_state(probs, 1e-6, opt)
+    dims = np.array([math.comb(om, n) for om, n, _, _ in probs])
+    order = np.argsort(dims)
+    picks = [int(order[k]) for k in np.linspace(0, len(order) - 1, 12).astype(int)]
+    for i in picks:
+        om, n, e, G = probs[i]
+        if dims[i] <= 20000:
+            ref = oracle.lanczos_ground(om, n, e, G, window=40, tol=1e-12)["e0"]
+        else:
+            with pd.Solver(om, n, e, G) as s:
+                ref = s.ground_state(1e-11, want_vector=False)["e0"]
+        assert abs(r["e0"][i] - ref) <= 1e-8 * max(1.0, abs(ref)), (i, om, n, dims[i])
+    assert np.mean(r["converged"]) >= 0.99
