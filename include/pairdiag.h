@@ -55,6 +55,8 @@ extern "C" {
 #define PD_START_FIRST  1  /* [1,0,...,0]^T, the paper's default (Sec. 3.4) */
 #define PD_START_HF     2  /* unit vector on the state of lowest diagonal element */
 #define PD_START_USER   3  /* caller-provided vector (pairdiag_set_start) */
+#define PD_START_MLP    4  /* product vector exp(sum_{i in s} w_i) with w from the learned
+                              network (pairdiag_set_mlp) or given (pairdiag_set_start_weights) */
 
 typedef struct pairdiag pairdiag_t;   /* opaque; owned by the library */
 
@@ -184,6 +186,47 @@ int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec
  * normalised FP64 vector v_dev (device, [dim]); occ: host [omega].  Synchronous.
  */
 int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ);
+
+/* ------------------------------------------------ learned warm start ---- */
+/*
+ * The paper starts Lanczos from [1,0,...,0] (Sec. 3.4) and has no learned
+ * component; this warm start is an addition of this library.  A network maps
+ * per-orbit features of (e, G, N) to weights w_i; the start vector is
+ * psi(s) = exp(sum_{i in s} w_i - max).  Network: 16 -> 128 -> 128 -> 128 -> 1,
+ * SiLU, bfloat16 operands with FP32 accumulation, FP32 master weights, Adam.
+ * Parameters (pairdiag_mlp_num_params() floats) are packed as W1 [16x128],
+ * b1 [128], W2 [128x128], b2, W3 [128x128], b3, w4 [128], b4 [1], row-major.
+ */
+typedef struct pairdiag_mlp pairdiag_mlp_t;
+
+/* New network with seeded initial weights on the current device. */
+int  pairdiag_mlp_create(uint64_t seed, pairdiag_mlp_t **out);
+void pairdiag_mlp_destroy(pairdiag_mlp_t *m);
+int  pairdiag_mlp_num_params(void);
+/* Copy the FP32 parameters out / in (host [num_params]); set resets Adam. */
+int  pairdiag_mlp_get_params(const pairdiag_mlp_t *m, float *out);
+int  pairdiag_mlp_set_params(pairdiag_mlp_t *m, const float *in);
+/* Per-orbit input features of a problem: X host [omega x 16] floats. */
+int  pairdiag_mlp_features(int omega, int n_pairs, const double *e, const double *G, float *X);
+/* Network outputs for `rows` feature rows (host X [rows x 16] -> out [rows]). */
+int  pairdiag_mlp_forward(pairdiag_mlp_t *m, int rows, const float *X, float *out);
+/* One forward and backward pass: mean squared error against target [rows] and
+ * its gradient (host [num_params]).  Test hook of the training kernels. */
+int  pairdiag_mlp_loss_grad(pairdiag_mlp_t *m, int rows, const float *X, const float *target,
+                            double *loss, float *grad);
+/* `steps` full-batch Adam steps on (X, target); loss_history host [steps], nullable. */
+int  pairdiag_mlp_train(pairdiag_mlp_t *m, int rows, const float *X, const float *target, int steps,
+                        double lr, double *loss_history);
+/* Use the network for PD_START_MLP (the handle keeps the pointer; nullptr clears). */
+int  pairdiag_set_mlp(pairdiag_t *h, pairdiag_mlp_t *m);
+/* Use fixed weights w (host [omega]) for PD_START_MLP when no network is set. */
+int  pairdiag_set_start_weights(pairdiag_t *h, const double *w);
+/* Training target: the per-orbit weights w (host [omega], mean zero) that
+ * minimise sum_s v_s^2 (log|v_s| - sum_{i in s} w_i)^2 for a normalised FP64
+ * vector v_dev (device [dim]).  Synchronous. */
+int  pairdiag_product_fit(pairdiag_t *h, const double *v_dev, double *w);
+/* The product vector exp(sum_{i in s} w_i - max) into v_dev (device [dim], FP64). */
+int  pairdiag_product_start_dev(pairdiag_t *h, const double *w, double *v_dev);
 
 /* ------------------------------------------------------------- batch ---- */
 

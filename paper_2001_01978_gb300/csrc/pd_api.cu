@@ -111,6 +111,8 @@ struct pairdiag {
     void *d_p[2] = {nullptr, nullptr};
     double *d_v64 = nullptr, *d_w64 = nullptr;
     std::vector<double> start;
+    std::vector<double> start_w;     // per-orbit weights of a product start vector
+    pairdiag_mlp *mlp = nullptr;     // network predicting them (PD_START_MLP)
     // optional event timing of H*x launches
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> hx_events;
@@ -399,6 +401,14 @@ int init_start(pairdiag *h, int dtype)
         PD_CUDA(cudaStreamSynchronize(h->st));
         break;
     }
+    case PD_START_MLP: {
+        std::vector<double> w(h->omega);
+        if (h->mlp) PD_TRY(mlp_predict(h->mlp, h->omega, h->n, h->e.data(), h->G.data(), w.data()));
+        else if ((int)h->start_w.size() == h->omega) w = h->start_w;
+        else return fail(PD_EINVAL, "PD_START_MLP needs pairdiag_set_mlp or pairdiag_set_start_weights");
+        PD_TRY(product_start(h->B, w.data(), dtype, q0, h->st));
+        break;
+    }
     case PD_START_USER: {
         if ((int64_t)h->start.size() != dim) return fail(PD_EINVAL, "no start vector set (pairdiag_set_start)");
         PD_TRY(ensure_fp64_pair(h));
@@ -580,6 +590,7 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     if (o.low_bits < 0 || o.low_bits > kMaxLow) return fail(PD_EINVAL, "low_bits outside 0..%d", kMaxLow);
     if (o.max_restarts < 0) return fail(PD_EINVAL, "max_restarts < 0");
     if (o.hx_variant < 0 || o.hx_variant > 2) return fail(PD_EINVAL, "hx_variant outside 0..2");
+    if (o.start < PD_START_RANDOM || o.start > PD_START_MLP) return fail(PD_EINVAL, "bad start kind");
 
     pairdiag *h = new pairdiag();
     h->omega = omega; h->n = n_pairs; h->opt = o;
@@ -726,6 +737,32 @@ int pairdiag_monopole(pairdiag_t *h, double *dmin, double *dmax, int64_t *pos_mi
     memcpy(&pos, &out[2], sizeof pos);
     *pos_min = pos;
     return PD_OK;
+}
+
+int pairdiag_set_mlp(pairdiag_t *h, pairdiag_mlp_t *m)
+{
+    if (!h) return fail(PD_EINVAL, "null handle");
+    h->mlp = m;
+    return PD_OK;
+}
+
+int pairdiag_set_start_weights(pairdiag_t *h, const double *w)
+{
+    if (!h || !w) return fail(PD_EINVAL, "null argument");
+    h->start_w.assign(w, w + h->omega);
+    return PD_OK;
+}
+
+int pairdiag_product_fit(pairdiag_t *h, const double *v_dev, double *w)
+{
+    if (!h || !v_dev || !w) return fail(PD_EINVAL, "null argument");
+    return product_fit(h->B, v_dev, w, h->st);
+}
+
+int pairdiag_product_start_dev(pairdiag_t *h, const double *w, double *v_dev)
+{
+    if (!h || !w || !v_dev) return fail(PD_EINVAL, "null argument");
+    return product_start(h->B, w, 0, v_dev, h->st);
 }
 
 int pairdiag_set_start(pairdiag_t *h, const double *v)

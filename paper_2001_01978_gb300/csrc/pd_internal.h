@@ -11,6 +11,7 @@
 // base(h) is the sum of C(L + p_j, ordinal_j) over the set bits of h (ordinals
 // k+1..N).  Both parts are the paper's hash (Sec. 3.2) split at bit L.
 #pragma once
+struct pairdiag_mlp;
 #include <atomic>
 #include <cstdint>
 #include <vector>
@@ -220,5 +221,13 @@ cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, int last_c
                                 cudaStream_t st);
 // e0 = c2[0] / c2[1] (Rayleigh quotient from v^T w and v^T v)
 cudaError_t batch_rayleigh_launch(BatchState *S, int count, int stage, cudaStream_t st);
+
+// ---- learned warm start (pd_mlp.cu) ----------------------------------------------
+void mlp_features(int omega, int n, const double *e, const double *G, float *X);   // [omega x 16]
+// start vector v[s] = exp(sum_{p in s} w_p - max) on storage type dtype (synchronous)
+int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st);
+// weighted least-squares per-orbit weights of a normalised FP64 vector (synchronous)
+int product_fit(const Blocks &B, const double *v, double *w_out, cudaStream_t st);
+int mlp_predict(struct ::pairdiag_mlp *m, int omega, int n, const double *e, const double *G, double *w_out);
 
 }  // namespace pd

@@ -1,0 +1,693 @@
+// pd_mlp.cu -- the learned Lanczos warm start.
+//
+// A small network maps per-orbit features of a problem (e, G, N) to one weight
+// w_i per orbit; the start vector is psi(s) = exp(sum_{i in s} w_i), a product
+// over the occupied orbits of each basis state (the form of a number-projected
+// BCS state, which is close to the exact pairing ground state).  Training
+// targets come from ground states computed by this solver: for each training
+// problem, w* minimises sum_s psi(s)^2 (log|psi(s)| - sum_{i in s} w_i)^2.
+//
+// Network: 16 -> 128 -> 128 -> 128 -> 1, SiLU, bfloat16 operands with FP32
+// accumulation on the tensor cores (mma.sync m16n8k16), FP32 master weights,
+// Adam.  Sizes are tiny (rows = orbits of the training problems), so one tiled
+// kernel serves every product of the forward and backward passes.
+#include "pd_internal.h"
+#include "../../include/pairdiag.h"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+using namespace pd;
+
+namespace {
+
+constexpr int kF = 16, kH = 128;
+constexpr int oW1 = 0, ob1 = oW1 + kF * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+              ob3 = oW3 + kH * kH, ow4 = ob3 + kH, ob4 = ow4 + kH, kNParams = ob4 + 1;
+
+using bf16 = __nv_bfloat16;
+
+// ---- C[M,N] (+)= op(A)[M,K] op(B)[K,N], bfloat16 operands, FP32 accumulation --
+// A(m,k) = TA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n].
+// 64x64 tile per CTA (4 warps of 32x32), K split over gridDim.z with atomic adds.
+constexpr int kTM = 64, kTN = 64, kBK = 16, kPad = 8;
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                 "{%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+gemm_kernel(int M, int N, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
+            float *__restrict__ C, int ldc, int accumulate)
+{
+    __shared__ __align__(16) bf16 As[kTM][kBK + kPad];
+    __shared__ __align__(16) bf16 Bs[kTN][kBK + kPad];
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+    const int kchunk = ((K + gridDim.z - 1) / gridDim.z + kBK - 1) / kBK * kBK;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+        for (int idx = tid; idx < kTM * kBK; idx += 128) {
+            const int m = idx / kBK, k = idx % kBK, gm = m0 + m, gk = k0 + k;
+            As[m][k] = (gm < M && gk < kend) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : zero;
+        }
+        for (int idx = tid; idx < kTN * kBK; idx += 128) {
+            const int n = idx / kBK, k = idx % kBK, gn = n0 + n, gk = k0 + k;
+            Bs[n][k] = (gn < N && gk < kend) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : zero;
+        }
+        __syncthreads();
+        uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm + i * 16 + g;
+            af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][tq * 2]);
+            af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][tq * 2]);
+            af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][tq * 2 + 8]);
+            af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][tq * 2 + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = wn + j * 8 + g;
+            bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][tq * 2]);
+            bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][tq * 2 + 8]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
+        __syncthreads();
+    }
+    const bool atomic = gridDim.z > 1;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int r = m0 + wm + i * 16 + g + (c >= 2 ? 8 : 0);
+                const int col = n0 + wn + j * 8 + tq * 2 + (c & 1);
+                if (r < M && col < N) {
+                    float *dst = C + (size_t)r * ldc + col;
+                    if (atomic) atomicAdd(dst, acc[i][j][c]);
+                    else *dst = accumulate ? *dst + acc[i][j][c] : acc[i][j][c];
+                }
+            }
+}
+
+template <bool TA, bool TB>
+void gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, float *C, int ldc, int ksplit,
+          cudaStream_t st)
+{
+    dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, ksplit);
+    if (ksplit > 1) cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * ldc, st);
+    gemm_kernel<TA, TB><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, 0);
+    count_launches(1);
+}
+
+// ---- elementwise pieces ------------------------------------------------------
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z)
+{
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// Z += bias (in place, FP32), A = silu(Z) in bfloat16
+__global__ void bias_silu_kernel(float *__restrict__ Z, const float *__restrict__ bias, bf16 *__restrict__ Aout,
+                                 int rows)
+{
+    const int64_t n = (int64_t)rows * kH;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[i] + bias[i % kH];
+        Z[i] = z;
+        Aout[i] = __float2bfloat16(silu(z));
+    }
+}
+
+// out[r] = A3[r,:] . w4 + b4 (one warp per row)
+__global__ void head_kernel(const bf16 *__restrict__ A3, const bf16 *__restrict__ w4, const float *__restrict__ b4,
+                            float *__restrict__ out, int rows)
+{
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.0f;
+    for (int j = lane; j < kH; j += 32) s += __bfloat162float(A3[(size_t)r * kH + j]) * __bfloat162float(w4[j]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s + b4[0];
+}
+
+// dout = 2 (out - t) / rows; loss partial sums
+__global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ t, float *__restrict__ dout,
+                            int rows, double *__restrict__ loss)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const float d = out[r] - t[r];
+        dout[r] = 2.0f * d / (float)rows;
+        acc += (double)d * d;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, sh[0] / rows);
+}
+
+// head backward: g_w4[j] = sum_r A3[r,j] dout[r], g_b4 = sum dout; dZ3 = dout w4 silu'(Z3)
+__global__ void head_back_kernel(const bf16 *__restrict__ A3, const float *__restrict__ Z3, const bf16 *__restrict__ w4,
+                                 const float *__restrict__ dout, int rows, float *__restrict__ gw4,
+                                 float *__restrict__ gb4, bf16 *__restrict__ dZ, float *__restrict__ gb3)
+{
+    const int j = threadIdx.x;                 // column (blockDim.x == kH)
+    float sw = 0.0f, sb = 0.0f, sz = 0.0f;
+    const float wj = __bfloat162float(w4[j]);
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float d = dout[r];
+        const size_t i = (size_t)r * kH + j;
+        sw += __bfloat162float(A3[i]) * d;
+        if (j == 0) sb += d;
+        const float dz = d * wj * dsilu(Z3[i]);
+        dZ[i] = __float2bfloat16(dz);
+        sz += dz;
+    }
+    atomicAdd(&gw4[j], sw);
+    atomicAdd(&gb3[j], sz);
+    if (j == 0) atomicAdd(gb4, sb);
+}
+
+// dZ = dA silu'(Z) (dA FP32 from a product), bias gradient column sums
+__global__ void dsilu_kernel(const float *__restrict__ dA, const float *__restrict__ Z, int rows,
+                             bf16 *__restrict__ dZ, float *__restrict__ gb)
+{
+    const int j = threadIdx.x;
+    float sz = 0.0f;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const size_t i = (size_t)r * kH + j;
+        const float dz = dA[i] * dsilu(Z[i]);
+        dZ[i] = __float2bfloat16(dz);
+        sz += dz;
+    }
+    atomicAdd(&gb[j], sz);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ src, bf16 *__restrict__ dst, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16(src[i]);
+}
+
+__global__ void adam_kernel(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m1,
+                            float *__restrict__ m2, int n, float lr, float b1, float b2, float c1, float c2, float eps)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.0f - b1) * gi;
+        const float v = b2 * m2[i] + (1.0f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = v;
+        th[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+}  // namespace
+
+// ---- the network handle ----------------------------------------------------------
+struct pairdiag_mlp {
+    float *theta = nullptr;      // FP32 master parameters
+    bf16 *wb = nullptr;          // bfloat16 copies (same layout)
+    float *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    int cap = 0;                 // rows the work buffers hold
+    bf16 *X = nullptr, *A1 = nullptr, *A2 = nullptr, *A3 = nullptr, *dZ = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dA = nullptr, *out = nullptr, *t = nullptr, *dout = nullptr;
+    double *loss = nullptr;
+    int steps = 0;
+    cudaStream_t st = nullptr;
+};
+
+namespace {
+
+void mlp_free_work(pairdiag_mlp *m)
+{
+    void *p[] = {m->X, m->A1, m->A2, m->A3, m->dZ, m->Z1, m->Z2, m->Z3, m->dA, m->out, m->t, m->dout};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    m->X = m->A1 = m->A2 = m->A3 = m->dZ = nullptr;
+    m->Z1 = m->Z2 = m->Z3 = m->dA = m->out = m->t = m->dout = nullptr;
+    m->cap = 0;
+}
+
+int mlp_reserve(pairdiag_mlp *m, int rows)
+{
+    if (rows <= m->cap) return PD_OK;
+    mlp_free_work(m);
+    const size_t nh = (size_t)rows * kH;
+    PD_CUDA(cudaMalloc(&m->X, sizeof(bf16) * (size_t)rows * kF));
+    PD_CUDA(cudaMalloc(&m->A1, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->A2, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->A3, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->dZ, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->Z1, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->Z2, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->Z3, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->dA, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->out, sizeof(float) * rows));
+    PD_CUDA(cudaMalloc(&m->t, sizeof(float) * rows));
+    PD_CUDA(cudaMalloc(&m->dout, sizeof(float) * rows));
+    m->cap = rows;
+    return PD_OK;
+}
+
+int grid1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+// forward pass on m->X (rows x 16, bfloat16) -> m->out
+int mlp_forward(pairdiag_mlp *m, int rows)
+{
+    cudaStream_t st = m->st;
+    to_bf16_kernel<<<grid1(kNParams), 256, 0, st>>>(m->theta, m->wb, kNParams);
+    gemm<false, false>(rows, kH, kF, m->X, kF, m->wb + oW1, kH, m->Z1, kH, 1, st);
+    bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z1, m->theta + ob1, m->A1, rows);
+    gemm<false, false>(rows, kH, kH, m->A1, kH, m->wb + oW2, kH, m->Z2, kH, 1, st);
+    bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z2, m->theta + ob2, m->A2, rows);
+    gemm<false, false>(rows, kH, kH, m->A2, kH, m->wb + oW3, kH, m->Z3, kH, 1, st);
+    bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z3, m->theta + ob3, m->A3, rows);
+    head_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(m->A3, m->wb + ow4, m->theta + ob4, m->out, rows);
+    count_launches(5);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// loss and gradient (after mlp_forward) -> m->grad, m->loss
+int mlp_backward(pairdiag_mlp *m, int rows)
+{
+    cudaStream_t st = m->st;
+    const int ks = std::max(1, std::min(64, rows / 256));
+    PD_CUDA(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNParams, st));
+    PD_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
+    loss_kernel<<<std::max(1, std::min(64, (rows + 255) / 256)), 256, 0, st>>>(m->out, m->t, m->dout, rows, m->loss);
+    const int gr = std::max(1, std::min(1024, rows));
+    head_back_kernel<<<gr, kH, 0, st>>>(m->A3, m->Z3, m->wb + ow4, m->dout, rows, m->grad + ow4, m->grad + ob4,
+                                        m->dZ, m->grad + ob3);
+    // layer 3: gW3 = A2^T dZ3 (written straight into the gradient), dA2 = dZ3 W3^T
+    gemm<true, false>(kH, kH, rows, m->A2, kH, m->dZ, kH, m->grad + oW3, kH, ks, st);
+    gemm<false, true>(rows, kH, kH, m->dZ, kH, m->wb + oW3, kH, m->dA, kH, 1, st);
+    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA, m->Z2, rows, m->dZ, m->grad + ob2);
+    // layer 2
+    gemm<true, false>(kH, kH, rows, m->A1, kH, m->dZ, kH, m->grad + oW2, kH, ks, st);
+    gemm<false, true>(rows, kH, kH, m->dZ, kH, m->wb + oW2, kH, m->dA, kH, 1, st);
+    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA, m->Z1, rows, m->dZ, m->grad + ob1);
+    // layer 1: gW1 = X^T dZ1
+    gemm<true, false>(kF, kH, rows, m->X, kF, m->dZ, kH, m->grad + oW1, kH, ks, st);
+    count_launches(4);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int mlp_load_inputs(pairdiag_mlp *m, int rows, const float *X, const float *t)
+{
+    PD_TRY(mlp_reserve(m, rows));
+    std::vector<bf16> xb((size_t)rows * kF);
+    for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16(X[i]);
+    PD_CUDA(cudaMemcpyAsync(m->X, xb.data(), sizeof(bf16) * xb.size(), cudaMemcpyHostToDevice, m->st));
+    if (t) PD_CUDA(cudaMemcpyAsync(m->t, t, sizeof(float) * rows, cudaMemcpyHostToDevice, m->st));
+    PD_CUDA(cudaStreamSynchronize(m->st));          // host staging buffers go out of scope
+    return PD_OK;
+}
+
+// ---- start vector and target fit over the basis blocks ---------------------------
+// v[s] = exp(sum_{p in s} w_p - shift)
+template <typename T>
+__global__ void __launch_bounds__(256)
+product_start_kernel(const Blocks B, const double *__restrict__ w, double shift, T *__restrict__ v)
+{
+    __shared__ double sw[kMaxOmega];
+    for (int p = threadIdx.x; p < B.omega; p += blockDim.x) sw[p] = w[p];
+    __syncthreads();
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        int off = 0;
+        for (int j = 0; j < k; ++j) off += (int)B.binom[B.L * kBinomStride + j];
+        const uint16_t *lw = B.lowword + off;
+        double sh = -shift;
+        for (uint64_t m = h; m; m &= m - 1) sh += sw[B.L + __ffsll((long long)m) - 1];
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            double s = sh;
+            for (uint32_t m = lw[r]; m; m &= m - 1) s += sw[__ffs(m) - 1];
+            v[base + r] = (T)exp(s);
+        }
+    }
+}
+
+// per CTA: M[i][j] += psi^2 n_i n_j, b[i] += psi^2 n_i log|psi| (shared accumulators)
+__global__ void __launch_bounds__(256)
+fit_kernel(const Blocks B, const double *__restrict__ v, double *__restrict__ part)
+{
+    extern __shared__ double acc[];              // omega*omega + omega
+    const int om = B.omega, nacc = om * om + om;
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        int off = 0;
+        for (int j = 0; j < k; ++j) off += (int)B.binom[B.L * kBinomStride + j];
+        const uint16_t *lw = B.lowword + off;
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            const double x = v[base + r];
+            const double w2 = x * x;
+            if (!(w2 > 1e-300)) continue;
+            const double lg = log(fabs(x));
+            const uint64_t s = (h << B.L) | (uint64_t)lw[r];
+            for (uint64_t mi = s; mi; mi &= mi - 1) {
+                const int i = __ffsll((long long)mi) - 1;
+                atomicAdd(&acc[om * om + i], w2 * lg);
+                for (uint64_t mj = s; mj; mj &= mj - 1) atomicAdd(&acc[i * om + __ffsll((long long)mj) - 1], w2);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x) part[(size_t)blockIdx.x * nacc + i] = acc[i];
+}
+
+__global__ void fit_sum_kernel(const double *__restrict__ part, int nparts, int nacc, double *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nacc; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * nacc + i];
+        out[i] = s;
+    }
+}
+
+}  // namespace
+
+namespace pd {
+
+// Per-orbit features of a problem (host): the Fermi level lam between the N-th
+// and (N+1)-th lowest d_p = 2 e_p + G_pp, the pairing scale g = mean |G_ij|
+// (i != j), the spread of d.
+void mlp_features(int omega, int n, const double *e, const double *G, float *X)
+{
+    std::vector<double> d(omega);
+    for (int p = 0; p < omega; ++p) d[p] = 2.0 * e[p] + G[p * omega + p];
+    std::vector<int> order(omega);
+    for (int p = 0; p < omega; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
+    std::vector<int> rank(omega);
+    for (int r = 0; r < omega; ++r) rank[order[r]] = r;
+    const double lo = n > 0 ? d[order[n - 1]] : d[order[0]] - 1.0;
+    const double hi = n < omega ? d[order[n]] : d[order[omega - 1]] + 1.0;
+    const double lam = 0.5 * (lo + hi);
+    double g = 0.0, mean = 0.0, var = 0.0;
+    for (int i = 0; i < omega; ++i)
+        for (int j = 0; j < omega; ++j)
+            if (i != j) g += std::fabs(G[i * omega + j]);
+    g = omega > 1 ? g / (omega * (omega - 1.0)) : 1.0;
+    if (!(g > 0.0)) g = 1.0;
+    for (int p = 0; p < omega; ++p) mean += d[p];
+    mean /= omega;
+    for (int p = 0; p < omega; ++p) var += (d[p] - mean) * (d[p] - mean);
+    const double sd = std::sqrt(var / omega) + 1e-12;
+    for (int p = 0; p < omega; ++p) {
+        double row = 0.0;
+        for (int j = 0; j < omega; ++j)
+            if (j != p) row += G[p * omega + j];
+        row = omega > 1 ? row / (omega - 1.0) : 0.0;
+        float *x = X + (size_t)p * kF;
+        const double u = (d[p] - lam) / g;
+        x[0] = (float)(u / 10.0);
+        x[1] = (float)std::tanh(u / omega);
+        x[2] = rank[p] < n ? 1.0f : 0.0f;
+        x[3] = (float)(G[p * omega + p] / g);
+        x[4] = (float)(row / g);
+        x[5] = (float)((double)n / omega);
+        x[6] = (float)(omega / 32.0);
+        x[7] = (float)((rank[p] - n + 0.5) / omega);
+        x[8] = (float)((d[p] - lam) / sd);
+        x[9] = (float)(g / sd);
+        x[10] = (float)std::tanh(u);
+        x[11] = (float)std::tanh(u / 4.0);
+        for (int f = 12; f < kF; ++f) x[f] = 0.0f;
+    }
+}
+
+// weights w (host, [omega]) -> start vector (device) of storage dtype
+int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st)
+{
+    std::vector<double> w(w_host, w_host + B.omega);
+    std::vector<double> srt(w);
+    std::sort(srt.begin(), srt.end(), std::greater<double>());
+    double shift = 0.0;
+    for (int i = 0; i < B.n; ++i) shift += srt[i];        // the largest exponent over the basis
+    double *dw = nullptr;
+    PD_CUDA(cudaMalloc(&dw, sizeof(double) * B.omega));
+    cudaError_t e = cudaMemcpyAsync(dw, w.data(), sizeof(double) * B.omega, cudaMemcpyHostToDevice, st);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, 152 * 4));
+    if (e == cudaSuccess) {
+        if (dtype == 0) product_start_kernel<double><<<grid, 256, 0, st>>>(B, dw, shift, (double *)v);
+        else product_start_kernel<float><<<grid, 256, 0, st>>>(B, dw, shift, (float *)v);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dw);
+    PD_CUDA(e);
+    return PD_OK;
+}
+
+// least-squares per-orbit weights of a normalised FP64 vector v (device)
+int product_fit(const Blocks &B, const double *v, double *w_out, cudaStream_t st)
+{
+    const int om = B.omega, nacc = om * om + om;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, 152 * 2));
+    double *part = nullptr, *sum = nullptr;
+    PD_CUDA(cudaMalloc(&part, sizeof(double) * (size_t)grid * nacc));
+    cudaError_t e = cudaMalloc(&sum, sizeof(double) * nacc);
+    std::vector<double> h(nacc);
+    if (e == cudaSuccess) {
+        const size_t smem = sizeof(double) * nacc;
+        cudaFuncSetAttribute(fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fit_kernel<<<grid, 256, smem, st>>>(B, v, part);
+        fit_sum_kernel<<<(nacc + 255) / 256, 256, 0, st>>>(part, grid, nacc, sum);
+        count_launches(2);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), sum, sizeof(double) * nacc, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(part);
+    if (sum) cudaFree(sum);
+    PD_CUDA(e);
+    // solve (M + eps I) w = b by Gaussian elimination with partial pivoting
+    std::vector<double> M(h.begin(), h.begin() + om * om), b(h.begin() + om * om, h.end());
+    double tr = 0.0;
+    for (int i = 0; i < om; ++i) tr += M[i * om + i];
+    for (int i = 0; i < om; ++i) M[i * om + i] += 1e-9 * (tr / om + 1e-300);   // ridge: orbits that are
+                                                                                // (almost) always full or empty
+    for (int c = 0; c < om; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < om; ++r)
+            if (std::fabs(M[r * om + c]) > std::fabs(M[piv * om + c])) piv = r;
+        if (piv != c) {
+            for (int j = 0; j < om; ++j) std::swap(M[c * om + j], M[piv * om + j]);
+            std::swap(b[c], b[piv]);
+        }
+        const double dv = M[c * om + c];
+        if (dv == 0.0) return fail(PD_ECUDA, "product fit: singular normal equations");
+        for (int r = c + 1; r < om; ++r) {
+            const double f = M[r * om + c] / dv;
+            if (f == 0.0) continue;
+            for (int j = c; j < om; ++j) M[r * om + j] -= f * M[c * om + j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = om - 1; c >= 0; --c) {
+        double s = b[c];
+        for (int j = c + 1; j < om; ++j) s -= M[c * om + j] * w_out[j];
+        w_out[c] = s / M[c * om + c];
+    }
+    double mean = 0.0;                               // remove the free constant (a global scale)
+    for (int i = 0; i < om; ++i) mean += w_out[i];
+    mean /= om;
+    for (int i = 0; i < om; ++i) w_out[i] -= mean;
+    return PD_OK;
+}
+
+int mlp_predict(pairdiag_mlp *m, int omega, int n, const double *e, const double *G, double *w_out)
+{
+    std::vector<float> X((size_t)omega * kF);
+    mlp_features(omega, n, e, G, X.data());
+    PD_TRY(mlp_load_inputs(m, omega, X.data(), nullptr));
+    PD_TRY(mlp_forward(m, omega));
+    std::vector<float> o(omega);
+    PD_CUDA(cudaMemcpyAsync(o.data(), m->out, sizeof(float) * omega, cudaMemcpyDeviceToHost, m->st));
+    PD_CUDA(cudaStreamSynchronize(m->st));
+    for (int i = 0; i < omega; ++i) w_out[i] = o[i];
+    return PD_OK;
+}
+
+}  // namespace pd
+
+extern "C" {
+
+int pairdiag_mlp_create(uint64_t seed, pairdiag_mlp_t **out)
+{
+    if (!out) return fail(PD_EINVAL, "null argument");
+    *out = nullptr;
+    pairdiag_mlp *m = new pairdiag_mlp();
+    // He-style initialisation from a counter-based generator
+    std::vector<float> th(kNParams, 0.0f);
+    auto uni = [&](uint64_t i) {
+        uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    };
+    auto fill = [&](int off, int n, double scale) {
+        for (int i = 0; i < n; ++i) th[off + i] = (float)(scale * uni((uint64_t)(off + i)));
+    };
+    fill(oW1, kF * kH, std::sqrt(6.0 / kF));
+    fill(oW2, kH * kH, std::sqrt(6.0 / kH));
+    fill(oW3, kH * kH, std::sqrt(6.0 / kH));
+    fill(ow4, kH, std::sqrt(3.0 / kH));
+    int st = PD_OK;
+    do {
+        if (cudaMalloc(&m->theta, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMalloc(&m->wb, sizeof(bf16) * kNParams) != cudaSuccess ||
+            cudaMalloc(&m->grad, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMalloc(&m->m1, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMalloc(&m->m2, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMalloc(&m->loss, sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(PD_ENOMEM, "mlp: allocation failed");
+            break;
+        }
+        if (cudaMemcpy(m->theta, th.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(m->m1, 0, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMemset(m->m2, 0, sizeof(float) * kNParams) != cudaSuccess)
+            st = fail(PD_ECUDA, "mlp: initialisation failed");
+    } while (0);
+    if (st != PD_OK) {
+        pairdiag_mlp_destroy(m);
+        return st;
+    }
+    *out = m;
+    return PD_OK;
+}
+
+void pairdiag_mlp_destroy(pairdiag_mlp_t *m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->st);
+    mlp_free_work(m);
+    void *p[] = {m->theta, m->wb, m->grad, m->m1, m->m2, m->loss};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    delete m;
+}
+
+int pairdiag_mlp_num_params(void) { return kNParams; }
+
+int pairdiag_mlp_get_params(const pairdiag_mlp_t *m, float *out)
+{
+    if (!m || !out) return fail(PD_EINVAL, "null argument");
+    PD_CUDA(cudaMemcpy(out, m->theta, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+    return PD_OK;
+}
+
+int pairdiag_mlp_set_params(pairdiag_mlp_t *m, const float *in)
+{
+    if (!m || !in) return fail(PD_EINVAL, "null argument");
+    PD_CUDA(cudaMemcpy(m->theta, in, sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemset(m->m1, 0, sizeof(float) * kNParams));
+    PD_CUDA(cudaMemset(m->m2, 0, sizeof(float) * kNParams));
+    m->steps = 0;
+    return PD_OK;
+}
+
+int pairdiag_mlp_features(int omega, int n_pairs, const double *e, const double *G, float *X)
+{
+    if (omega < 1 || omega > kMaxOmega || n_pairs < 0 || n_pairs > omega || !e || !G || !X)
+        return fail(PD_EINVAL, "bad argument");
+    mlp_features(omega, n_pairs, e, G, X);
+    return PD_OK;
+}
+
+int pairdiag_mlp_forward(pairdiag_mlp_t *m, int rows, const float *X, float *out)
+{
+    if (!m || rows < 1 || !X || !out) return fail(PD_EINVAL, "bad argument");
+    PD_TRY(mlp_load_inputs(m, rows, X, nullptr));
+    PD_TRY(mlp_forward(m, rows));
+    PD_CUDA(cudaMemcpyAsync(out, m->out, sizeof(float) * rows, cudaMemcpyDeviceToHost, m->st));
+    PD_CUDA(cudaStreamSynchronize(m->st));
+    return PD_OK;
+}
+
+int pairdiag_mlp_loss_grad(pairdiag_mlp_t *m, int rows, const float *X, const float *target, double *loss,
+                           float *grad)
+{
+    if (!m || rows < 1 || !X || !target || !loss || !grad) return fail(PD_EINVAL, "bad argument");
+    PD_TRY(mlp_load_inputs(m, rows, X, target));
+    PD_TRY(mlp_forward(m, rows));
+    PD_TRY(mlp_backward(m, rows));
+    PD_CUDA(cudaMemcpyAsync(grad, m->grad, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, m->st));
+    PD_CUDA(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
+    PD_CUDA(cudaStreamSynchronize(m->st));
+    return PD_OK;
+}
+
+int pairdiag_mlp_train(pairdiag_mlp_t *m, int rows, const float *X, const float *target, int steps, double lr,
+                       double *loss_history)
+{
+    if (!m || rows < 1 || !X || !target || steps < 0 || !(lr > 0.0)) return fail(PD_EINVAL, "bad argument");
+    PD_TRY(mlp_load_inputs(m, rows, X, target));
+    const float b1 = 0.9f, b2 = 0.999f;
+    std::vector<double> hist(steps);
+    double *d_hist = nullptr;
+    if (loss_history && steps > 0) PD_CUDA(cudaMalloc(&d_hist, sizeof(double) * steps));
+    int rc = PD_OK;
+    for (int s = 0; s < steps && rc == PD_OK; ++s) {
+        rc = mlp_forward(m, rows);
+        if (rc == PD_OK) rc = mlp_backward(m, rows);
+        if (rc != PD_OK) break;
+        ++m->steps;
+        const float c1 = 1.0f - std::pow(b1, (float)m->steps), c2 = 1.0f - std::pow(b2, (float)m->steps);
+        adam_kernel<<<grid1(kNParams), 256, 0, m->st>>>(m->theta, m->grad, m->m1, m->m2, kNParams, (float)lr, b1, b2,
+                                                        c1, c2, 1e-8f);
+        count_launches(1);
+        if (d_hist) cudaMemcpyAsync(d_hist + s, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, m->st);
+    }
+    if (rc == PD_OK && d_hist) {
+        cudaMemcpyAsync(loss_history, d_hist, sizeof(double) * steps, cudaMemcpyDeviceToHost, m->st);
+    }
+    const cudaError_t e = cudaStreamSynchronize(m->st);
+    if (d_hist) cudaFree(d_hist);
+    if (rc != PD_OK) return rc;
+    PD_CUDA(e);
+    return PD_OK;
+}
+
+}  // extern "C"

@@ -16,7 +16,7 @@ from . import build as _build
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ENOCONV, PD_ETIMEOUT, PD_ECUDA, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 PD_PREC_FP64, PD_PREC_MIXED = 0, 1
-PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER = 0, 1, 2, 3
+PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER, PD_START_MLP = 0, 1, 2, 3, 4
 
 
 class pairdiag_options(ctypes.Structure):
@@ -77,6 +77,19 @@ _SIGNATURES = {
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
                                                    ctypes.POINTER(pairdiag_options), _P, _P, _P, _P]),
+    "pairdiag_mlp_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_H)]),
+    "pairdiag_mlp_destroy": (None, [_H]),
+    "pairdiag_mlp_num_params": (ctypes.c_int, []),
+    "pairdiag_mlp_get_params": (ctypes.c_int, [_H, _P]),
+    "pairdiag_mlp_set_params": (ctypes.c_int, [_H, _P]),
+    "pairdiag_mlp_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "pairdiag_mlp_forward": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
+    "pairdiag_mlp_loss_grad": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
+    "pairdiag_mlp_train": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P]),
+    "pairdiag_set_mlp": (ctypes.c_int, [_H, _H]),
+    "pairdiag_set_start_weights": (ctypes.c_int, [_H, _P]),
+    "pairdiag_product_fit": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_product_start_dev": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_multidot_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P,
                                                  ctypes.c_int64, _P, _P]),
 }
@@ -303,6 +316,86 @@ def pairdiag_get_profile(h, precision: int = PD_PREC_MIXED):
     ms = ctypes.c_double()
     _check(lib().pairdiag_get_profile(h, precision, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+# ------------------------------------------------------- learned warm start ---
+def pairdiag_mlp_create(seed: int = 0):
+    m = _H()
+    _check(lib().pairdiag_mlp_create(seed, ctypes.byref(m)))
+    return m
+
+
+def pairdiag_mlp_destroy(m) -> None:
+    lib().pairdiag_mlp_destroy(m)
+
+
+def pairdiag_mlp_num_params() -> int:
+    return int(lib().pairdiag_mlp_num_params())
+
+
+def pairdiag_mlp_get_params(m) -> np.ndarray:
+    out = np.empty(pairdiag_mlp_num_params(), dtype=np.float32)
+    _check(lib().pairdiag_mlp_get_params(m, _np_ptr(out)))
+    return out
+
+
+def pairdiag_mlp_set_params(m, theta) -> None:
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(lib().pairdiag_mlp_set_params(m, _np_ptr(theta)))
+
+
+def pairdiag_mlp_features(omega: int, n_pairs: int, e, G) -> np.ndarray:
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    X = np.empty((omega, 16), dtype=np.float32)
+    _check(lib().pairdiag_mlp_features(omega, n_pairs, _np_ptr(e), _np_ptr(G), _np_ptr(X)))
+    return X
+
+
+def pairdiag_mlp_forward(m, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    out = np.empty(len(X), dtype=np.float32)
+    _check(lib().pairdiag_mlp_forward(m, len(X), _np_ptr(X), _np_ptr(out)))
+    return out
+
+
+def pairdiag_mlp_loss_grad(m, X, target):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    loss = ctypes.c_double()
+    grad = np.empty(pairdiag_mlp_num_params(), dtype=np.float32)
+    _check(lib().pairdiag_mlp_loss_grad(m, len(X), _np_ptr(X), _np_ptr(t), ctypes.byref(loss), _np_ptr(grad)))
+    return loss.value, grad
+
+
+def pairdiag_mlp_train(m, X, target, steps: int, lr: float = 1e-3) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    hist = np.empty(steps, dtype=np.float64)
+    _check(lib().pairdiag_mlp_train(m, len(X), _np_ptr(X), _np_ptr(t), steps, lr, _np_ptr(hist)))
+    return hist
+
+
+def pairdiag_set_mlp(h, m) -> None:
+    _check(lib().pairdiag_set_mlp(h, m))
+
+
+def pairdiag_set_start_weights(h, w) -> None:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(lib().pairdiag_set_start_weights(h, _np_ptr(w)))
+
+
+def pairdiag_product_fit(h, v, omega: int) -> np.ndarray:
+    import torch
+    w = np.empty(omega, dtype=np.float64)
+    _check(lib().pairdiag_product_fit(h, _dev_ptr(v, torch.float64), _np_ptr(w)))
+    return w
+
+
+def pairdiag_product_start_dev(h, w, v) -> None:
+    import torch
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(lib().pairdiag_product_start_dev(h, _np_ptr(w), _dev_ptr(v, torch.float64)))
 
 
 # ------------------------------------------------------------ convenience ---

@@ -114,6 +114,26 @@ def batch_workload(count: int = 4096, seed: int = 5, omega_lo: int = 10, omega_h
     return probs
 
 
+def training_problems(count: int, seed: int, omega_lo: int = 10, omega_hi: int = 18):
+    """Problems for training the warm-start network: the mean-field batch
+    distribution restricted to Omega in [omega_lo, omega_hi], plus picket-fence
+    spectra with constant G drawn in [-1, -0.1] for every fifth problem."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(count):
+        omega = int(rng.integers(omega_lo, omega_hi + 1))
+        n = min(max(omega // 2 + int(rng.integers(-3, 4)), 1), omega - 1)
+        if i % 5 == 4:
+            e = np.arange(omega, dtype=np.float64) * float(rng.uniform(0.5, 2.0))
+            G = np.full((omega, omega), float(rng.uniform(-1.0, -0.1)))
+        else:
+            e = rng.uniform(-10.0, 10.0, size=omega)
+            g = rng.uniform(0.3, 0.7, size=omega)
+            G = -np.outer(g, g) + _sym_noise(rng, omega, 0.05)
+        probs.append((omega, n, e, G))
+    return probs
+
+
 def n_states(omega: int, n: int) -> int:
     """Number of pair configurations, for sizing buffers (math.comb)."""
     return math.comb(omega, n) if 0 <= n <= omega else 0
