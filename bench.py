@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--batch", action="store_true",
                     help="4096-problem mean-field workload: solves/s and per-solve latency (own JSON line)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--warm", action="store_true",
+                    help="Omega=30 workload: FP64 random start vs mixed + learned warm start (own JSON line)")
+    ap.add_argument("--train-problems", type=int, default=240)
     return ap.parse_args()
 
 
@@ -428,6 +431,62 @@ def run_hx_only(args):
     return 0
 
 
+def train_warm_start(count: int):
+    """One-off: train the warm-start network on ground states the solver computes
+    at Omega <= 18 (returns the network and the seconds it took)."""
+    from paper_2001_01978_gb300 import warmstart
+    t0 = time.perf_counter()
+    X, T = warmstart.training_set(pd_inputs.training_problems(count, seed=11, omega_lo=10, omega_hi=18))
+    ws = warmstart.WarmStart(seed=0)
+    hist = ws.train(X, T, steps=2500, lr=2e-3)
+    return ws, time.perf_counter() - t0, float(hist[0]), float(hist[-1]), len(X)
+
+
+def run_warm(args):
+    """Omega=30, N=15 (dim 1.55e8, seed 2): time-to-E0 and Lanczos iterations of
+    plain FP64 Lanczos from a random start vs the mixed form from the learned
+    warm start (and from a random start), same tolerance."""
+    import torch
+    import paper_2001_01978_gb300 as pd
+    torch.cuda.set_device(0)
+    ws, train_s, l0, l1, rows = train_warm_start(args.train_problems)
+    omega, n, e, G = pd_inputs.workload("omega30_n15_sepnoise_s2")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    forms = [("fp64_random", pd.PD_PREC_FP64, pd.PD_START_RANDOM),
+             ("mixed_random", pd.PD_PREC_MIXED, pd.PD_START_RANDOM),
+             ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP)]
+    out = {}
+    for name, prec, start in forms:
+        with pd.Solver(omega, n, e, G, precision=prec, start=start, window=args.window, seed=1) as s:
+            pd.pairdiag_set_stream(s.h, stream)
+            if start == pd.PD_START_MLP:
+                ws.attach(s.h)
+            times, r = [], None
+            for i in range(max(1, args.steps)):
+                flush.fill_(1.0)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                r = pd.pairdiag_ground_state_dev(s.h, args.tol, None)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+        out[name] = {"time_to_e0_ms": statistics.median(times), "iterations": r["iterations"],
+                     "hx_products": r["hx_products"], "e0": r["e0"], "rel_residual": r["rel_residual"],
+                     "status": r["status"]}
+    ref = out["fp64_random"]["e0"]
+    for v in out.values():
+        v["e0_rel_diff_vs_fp64"] = abs(v["e0"] - ref) / abs(ref)
+    print(json.dumps({"warm_start": True, "workload": "omega30_n15_sepnoise_s2", "dim": math.comb(omega, n),
+                      "tol": args.tol, "window": args.window, "steps": args.steps,
+                      "training": {"problems": args.train_problems, "rows": rows, "seconds": train_s,
+                                   "loss_first": l0, "loss_last": l1},
+                      "forms": out,
+                      "speedup_mixed_mlp_vs_fp64_random": out["fp64_random"]["time_to_e0_ms"] / out["mixed_mlp"]["time_to_e0_ms"]}))
+    ws.close()
+    return 0
+
+
 def run_batch(args):
     """Batched form: 4096 Hamiltonians (Omega ~ U{10..22}, N = Omega/2 +- U{0..3}) in
     one lock-step solve, mixed form vs plain FP64, same tolerance."""
@@ -439,17 +498,21 @@ def run_batch(args):
     nnz = sum(d * n * (om - n) for d, (om, n, _, _) in zip(dims, probs))
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ws, train_s, _, _, _ = train_warm_start(args.train_problems)
     out = {}
-    for name, prec in (("mixed", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
-        opt = pd.pairdiag_default_options(precision=prec, window=args.window)
+    for name, prec, start in (("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP),
+                              ("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM),
+                              ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)):
+        opt = pd.pairdiag_default_options(precision=prec, window=args.window, start=start)
+        mlp = ws.m if start == pd.PD_START_MLP else None
         for _ in range(max(1, args.warmup // 3)):
-            pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream)
+            pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream, mlp)
         times, res = [], None
         for _ in range(args.steps):
             flush.fill_(1.0)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            res = pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream)
+            res = pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream, mlp)
             ev1.record(stream)
             ev1.synchronize()
             times.append(ev0.elapsed_time(ev1))
@@ -465,8 +528,11 @@ def run_batch(args):
     print(json.dumps({"batch": True, "workload": "mean-field batch: %d problems, Omega ~ U{10..22}, seed 5" % len(probs),
                       "total_dim": int(sum(dims)), "nnz_offdiag_per_batched_hx": int(nnz), "tol": args.tol,
                       "window": args.window, "steps": args.steps, "l2": "flushed between steps",
-                      "mixed": out["mixed"], "fp64": out["fp64"],
-                      "speedup_mixed_vs_fp64": out["fp64"]["batch_ms"] / out["mixed"]["batch_ms"]}))
+                      "warm_start_training_s": train_s,
+                      "mixed_mlp": out["mixed_mlp"], "mixed": out["mixed"], "fp64": out["fp64"],
+                      "speedup_mixed_vs_fp64": out["fp64"]["batch_ms"] / out["mixed"]["batch_ms"],
+                      "speedup_mixed_mlp_vs_fp64": out["fp64"]["batch_ms"] / out["mixed_mlp"]["batch_ms"]}))
+    ws.close()
     return 0
 
 
@@ -474,6 +540,8 @@ def main():
     args = parse_args()
     if args.batch:
         return run_batch(args)
+    if args.warm:
+        return run_warm(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

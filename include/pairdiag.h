@@ -253,7 +253,9 @@ typedef struct {
  *   tol            : |beta_1/alpha_1| (Sec. 5.1); the mixed form refines every
  *                    vector in FP64 and reports that residual instead
  *   opt            : nullable; window, max_restarts, precision, seed, low_bits and
- *                    mixed_floor are used; start must be PD_START_RANDOM, mode 0
+ *                    mixed_floor are used; start PD_START_RANDOM or PD_START_MLP, mode 0
+ *   mlp            : the warm-start network for PD_START_MLP (else nullable); one
+ *                    network pass serves the orbits of all problems
  *   e0, status     : host [count] outputs (PD_OK or PD_ENOCONV per problem)
  *   results        : host [count], nullable
  *   stream         : cudaStream_t as void* (nullptr = legacy default stream)
@@ -263,7 +265,8 @@ typedef struct {
  */
 int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs, const double *e_all,
                                 const double *G_all, double tol, const pairdiag_options *opt,
-                                double *e0, int *status, pairdiag_batch_result *results, void *stream);
+                                pairdiag_mlp_t *mlp, double *e0, int *status,
+                                pairdiag_batch_result *results, void *stream);
 
 /* ------------------------------------------------------- diagnostics ---- */
 

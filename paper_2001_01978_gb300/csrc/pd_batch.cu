@@ -66,7 +66,8 @@ struct Graph {
 
 extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs, const double *e_all,
                                            const double *G_all, double tol, const pairdiag_options *opt_in,
-                                           double *e0, int *status, pairdiag_batch_result *results, void *stream)
+                                           pairdiag_mlp_t *mlp, double *e0, int *status,
+                                           pairdiag_batch_result *results, void *stream)
 {
     if (count < 1 || !omega || !n_pairs || !e_all || !G_all || !e0 || !status)
         return fail(PD_EINVAL, "batch: bad argument");
@@ -77,7 +78,9 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
     if (opt.window < 1 || opt.window > kMaxWindow) return fail(PD_EINVAL, "batch: window outside 1..%d", kMaxWindow);
     if (opt.precision != PD_PREC_FP64 && opt.precision != PD_PREC_MIXED) return fail(PD_EINVAL, "batch: bad precision");
     if (opt.mode != 0) return fail(PD_ENOTSUP, "batch: only the restarted mode is supported");
-    if (opt.start != PD_START_RANDOM) return fail(PD_ENOTSUP, "batch: only the random start is supported");
+    if (opt.start != PD_START_RANDOM && opt.start != PD_START_MLP)
+        return fail(PD_ENOTSUP, "batch: the start must be PD_START_RANDOM or PD_START_MLP");
+    if (opt.start == PD_START_MLP && !mlp) return fail(PD_EINVAL, "batch: PD_START_MLP needs a network");
     if (opt.low_bits < 0 || opt.low_bits > kMaxLow) return fail(PD_EINVAL, "batch: low_bits outside 0..%d", kMaxLow);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int dtype = opt.precision == PD_PREC_MIXED ? 1 : 0;
@@ -317,7 +320,10 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
         if (dtype == 1) {
             PD_TRY(buf.alloc(&Q32, 4 * (size_t)m * (size_t)total));
             PD_TRY(buf.alloc(&p32, 4 * (size_t)total));
-            PD_CUDA(seg_random_launch(1, V, Q32, opt.seed, st));
+            if (opt.start == PD_START_MLP)
+                PD_TRY(batch_mlp_start(mlp, BB, count, omega, n_pairs, e_all, G_all, 1, Q32, st));
+            else
+                PD_CUDA(seg_random_launch(1, V, Q32, opt.seed, st));
             // FP32 cycles aim a little below tol so that the FP64 residual of the
             // refined vector, which also carries the FP32 rounding, stays within tol
             PD_TRY(run_phase(1, Q32, p32, std::max(0.5 * tol, opt.mixed_floor), 1, opt.max_restarts));
@@ -346,7 +352,10 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
         } else {
             PD_TRY(buf.alloc(&Q64, 8 * (size_t)m * (size_t)total));
             PD_TRY(buf.alloc(&p64, 8 * (size_t)total));
-            PD_CUDA(seg_random_launch(0, V, Q64, opt.seed, st));
+            if (opt.start == PD_START_MLP)
+                PD_TRY(batch_mlp_start(mlp, BB, count, omega, n_pairs, e_all, G_all, 0, Q64, st));
+            else
+                PD_CUDA(seg_random_launch(0, V, Q64, opt.seed, st));
             PD_TRY(run_phase(0, Q64, p64, tol, 0, opt.max_restarts));
         }
         return PD_OK;

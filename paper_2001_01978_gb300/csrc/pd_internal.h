@@ -229,5 +229,8 @@ int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cud
 // weighted least-squares per-orbit weights of a normalised FP64 vector (synchronous)
 int product_fit(const Blocks &B, const double *v, double *w_out, cudaStream_t st);
 int mlp_predict(struct ::pairdiag_mlp *m, int omega, int n, const double *e, const double *G, double *w_out);
+// product start vectors of every problem of a batch from one network pass (synchronous)
+int batch_mlp_start(struct ::pairdiag_mlp *m, const BatchBlocks &BB, int count, const int *omega, const int *n_pairs,
+                    const double *e_all, const double *G_all, int dtype, void *v, cudaStream_t st);
 
 }  // namespace pd

@@ -402,9 +402,88 @@ __global__ void fit_sum_kernel(const double *__restrict__ part, int nparts, int 
     }
 }
 
+// batched product start: v[s] = exp(sum_{p in s} w[woff + p] - shift[problem])
+template <typename T>
+__global__ void __launch_bounds__(256)
+batch_product_start_kernel(const BatchBlocks BB, const double *__restrict__ w, const int *__restrict__ woff,
+                           const double *__restrict__ shift, T *__restrict__ v)
+{
+    for (long long b = blockIdx.x; b < BB.nblocks; b += gridDim.x) {
+        const int pr = (int)BB.blk_prob[b];
+        const BatchDesc dsc = BB.desc[pr];
+        const double *wp = w + woff[pr];
+        const uint64_t h = BB.blk_h[b], base = BB.blk_base[b];
+        const int L = dsc.L;
+        const int k = dsc.n - __popcll(h);
+        const int nk = (int)BB.binom[L * kBinomStride + k];
+        int off = 0;
+        for (int j = 0; j < k; ++j) off += (int)BB.binom[L * kBinomStride + j];
+        const uint16_t *lw = BB.lowword_all + dsc.tab_off + off;
+        double sh = -shift[pr];
+        for (uint64_t m = h; m; m &= m - 1) sh += wp[L + __ffsll((long long)m) - 1];
+        T *vp = v + dsc.vec_off + base;
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            double sum = sh;
+            for (uint32_t m = lw[r]; m; m &= m - 1) sum += wp[__ffs(m) - 1];
+            vp[r] = (T)exp(sum);
+        }
+    }
+}
+
 }  // namespace
 
 namespace pd {
+
+// Batched warm start: one network pass over the orbits of all problems, then the
+// product start vectors of every problem (storage dtype) into v (device).
+int batch_mlp_start(struct ::pairdiag_mlp *m, const BatchBlocks &BB, int count, const int *omega, const int *n_pairs,
+                    const double *e_all, const double *G_all, int dtype, void *v, cudaStream_t st)
+{
+    std::vector<int> woff(count);
+    int rows = 0;
+    for (int p = 0; p < count; ++p) { woff[p] = rows; rows += omega[p]; }
+    std::vector<float> X((size_t)rows * kF);
+    int64_t eo = 0, go = 0;
+    for (int p = 0; p < count; ++p) {
+        mlp_features(omega[p], n_pairs[p], e_all + eo, G_all + go, X.data() + (size_t)woff[p] * kF);
+        eo += omega[p];
+        go += (int64_t)omega[p] * omega[p];
+    }
+    PD_TRY(mlp_load_inputs(m, rows, X.data(), nullptr));
+    PD_TRY(mlp_forward(m, rows));
+    std::vector<float> o(rows);
+    PD_CUDA(cudaMemcpyAsync(o.data(), m->out, sizeof(float) * rows, cudaMemcpyDeviceToHost, m->st));
+    PD_CUDA(cudaStreamSynchronize(m->st));
+    std::vector<double> w(o.begin(), o.end()), shift(count);
+    for (int p = 0; p < count; ++p) {
+        std::vector<double> srt(w.begin() + woff[p], w.begin() + woff[p] + omega[p]);
+        std::sort(srt.begin(), srt.end(), std::greater<double>());
+        double sh = 0.0;
+        for (int i = 0; i < n_pairs[p]; ++i) sh += srt[i];
+        shift[p] = sh;
+    }
+    double *dw = nullptr, *dsh = nullptr;
+    int *dwo = nullptr;
+    PD_CUDA(cudaMalloc(&dw, sizeof(double) * rows));
+    cudaError_t e = cudaMalloc(&dsh, sizeof(double) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&dwo, sizeof(int) * count);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w.data(), sizeof(double) * rows, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsh, shift.data(), sizeof(double) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dwo, woff.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(BB.nblocks, 152 * 8));
+        if (dtype == 0) batch_product_start_kernel<double><<<grid, 256, 0, st>>>(BB, dw, dwo, dsh, (double *)v);
+        else batch_product_start_kernel<float><<<grid, 256, 0, st>>>(BB, dw, dwo, dsh, (float *)v);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dw);
+    if (dsh) cudaFree(dsh);
+    if (dwo) cudaFree(dwo);
+    PD_CUDA(e);
+    return PD_OK;
+}
 
 // Per-orbit features of a problem (host): the Fermi level lam between the N-th
 // and (N+1)-th lowest d_p = 2 e_p + G_pp, the pairing scale g = mean |G_ij|

@@ -76,7 +76,7 @@ _SIGNATURES = {
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
-                                                   ctypes.POINTER(pairdiag_options), _P, _P, _P, _P]),
+                                                   ctypes.POINTER(pairdiag_options), _H, _P, _P, _P, _P]),
     "pairdiag_mlp_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_H)]),
     "pairdiag_mlp_destroy": (None, [_H]),
     "pairdiag_mlp_num_params": (ctypes.c_int, []),
@@ -267,7 +267,8 @@ def pairdiag_multidot_noalloc(Q, ld: int, m: int, p, n: int, out, stream=None) -
                                            _dev_ptr(out, torch.float64), ctypes.c_void_p(sp)))
 
 
-def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | None = None, stream=None) -> dict:
+def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | None = None, stream=None,
+                                mlp=None) -> dict:
     """problems: sequence of (omega, n_pairs, e, G).  Returns per-problem arrays
     e0, status, iterations, converged, stalled, rel_residual, latency_ms and the
     call's status."""
@@ -281,7 +282,7 @@ def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | No
     res = (pairdiag_batch_result * count)()
     sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
     st = _check(lib().pairdiag_batch_ground_state(count, _np_ptr(om), _np_ptr(nn), _np_ptr(e_all), _np_ptr(G_all),
-                                                  tol, ctypes.byref(opt) if opt is not None else None,
+                                                  tol, ctypes.byref(opt) if opt is not None else None, mlp,
                                                   _np_ptr(e0), _np_ptr(status), ctypes.cast(res, ctypes.c_void_p),
                                                   ctypes.c_void_p(sp)), allow=(PD_OK, PD_ENOCONV))
     out = dict(e0=e0, status=status, call_status=st)
