@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--warm", action="store_true",
                     help="Omega=30 workload: FP64 random start vs mixed + learned warm start (own JSON line)")
     ap.add_argument("--train-problems", type=int, default=240)
+    ap.add_argument("--no-mlp", action="store_true", help="batch mode without the learned warm start")
     return ap.parse_args()
 
 
@@ -498,11 +499,12 @@ def run_batch(args):
     nnz = sum(d * n * (om - n) for d, (om, n, _, _) in zip(dims, probs))
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    ws, train_s, _, _, _ = train_warm_start(args.train_problems)
+    ws, train_s = (None, None) if args.no_mlp else train_warm_start(args.train_problems)[:2]
+    forms = [("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM), ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)]
+    if ws is not None:
+        forms.insert(0, ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP))
     out = {}
-    for name, prec, start in (("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP),
-                              ("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM),
-                              ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)):
+    for name, prec, start in forms:
         opt = pd.pairdiag_default_options(precision=prec, window=args.window, start=start)
         mlp = ws.m if start == pd.PD_START_MLP else None
         for _ in range(max(1, args.warmup // 3)):
@@ -529,10 +531,12 @@ def run_batch(args):
                       "total_dim": int(sum(dims)), "nnz_offdiag_per_batched_hx": int(nnz), "tol": args.tol,
                       "window": args.window, "steps": args.steps, "l2": "flushed between steps",
                       "warm_start_training_s": train_s,
-                      "mixed_mlp": out["mixed_mlp"], "mixed": out["mixed"], "fp64": out["fp64"],
+                      "mixed_mlp": out.get("mixed_mlp"), "mixed": out["mixed"], "fp64": out["fp64"],
                       "speedup_mixed_vs_fp64": out["fp64"]["batch_ms"] / out["mixed"]["batch_ms"],
-                      "speedup_mixed_mlp_vs_fp64": out["fp64"]["batch_ms"] / out["mixed_mlp"]["batch_ms"]}))
-    ws.close()
+                      "speedup_mixed_mlp_vs_fp64": (out["fp64"]["batch_ms"] / out["mixed_mlp"]["batch_ms"]
+                                                    if "mixed_mlp" in out else None)}))
+    if ws is not None:
+        ws.close()
     return 0
 
 

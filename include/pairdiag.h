@@ -296,11 +296,11 @@ int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, i
                       const void *p_dev, int64_t n, double *out);
 
 /*
- * Lowest (and second-lowest) eigenvalue and the lowest eigenvector of the
- * symmetric tridiagonal matrix with diagonal alpha[m] and off-diagonal
- * beta[m-1] (the L matrix of Algorithm 2; QR_Decompose in App. B), computed
- * by the device solver.  alpha, beta: host; theta: host [2]; s: host [m].
- * m <= 64.  Synchronous.
+ * Lowest eigenvalue (to FP64 accuracy), the second-lowest (to FP32 accuracy,
+ * a gap estimate) and the lowest eigenvector of the symmetric tridiagonal
+ * matrix with diagonal alpha[m] and off-diagonal beta[m-1] (the L matrix of
+ * Algorithm 2; QR_Decompose in App. B), computed by the device solver.
+ * alpha, beta: host; theta: host [2]; s: host [m].  m <= 64.  Synchronous.
  */
 int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const double *beta,
                             double *theta, double *s);

@@ -79,13 +79,47 @@ __device__ __forceinline__ void ff_add_prod(float &hi, float &lo, float a, float
     lo += e + pe;
 }
 
+// (ah, al) += (bh, bl) in float-float arithmetic (TwoSum, then renormalised)
+__device__ __forceinline__ void ff_add(float &ah, float &al, float bh, float bl)
+{
+    const float s = ah + bh;
+    const float z = s - ah;
+    float e = (ah - (s - z)) + (bh - z);
+    e += al + bl;
+    const float h = s + e;
+    al = e - (h - s);
+    ah = h;
+}
+
+// block-wide float-float sum, converted to double once (thread 0 holds it):
+// the whole reduction tree stays on the FP32 pipes
+__device__ __forceinline__ double block_sum_ff(float hi, float lo, float *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, oh, ol);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) { sh[2 * w] = hi; sh[2 * w + 1] = lo; }
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        float th = 0.0f, tl = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ff_add(th, tl, sh[2 * i], sh[2 * i + 1]);
+        r = (double)th + (double)tl;
+    }
+    return r;
+}
+
 // multi-dot of FP32 vectors, float-float per thread, FP64 across threads
 __global__ void __launch_bounds__(kThreads)
 multidot_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const float *__restrict__ p, int64_t n,
                     double *__restrict__ part, const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];
+    __shared__ float sh[2 * (kThreads / 32)];
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     for (int j0 = 0; j0 < m; j0 += kGroup) {
         float hi[kGroup], lo[kGroup];
@@ -100,7 +134,7 @@ multidot_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const float
 #pragma unroll
         for (int u = 0; u < kGroup; ++u) {
             if (j0 + u < m) {
-                const double s = block_sum((double)hi[u] + (double)lo[u], sh);
+                const double s = block_sum_ff(hi[u], lo[u], sh);
                 if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
             }
         }
@@ -118,7 +152,7 @@ recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosS
                      T *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kThreads / 32];          // also holds the float pairs of block_sum_ff
     const int m = i + 1;
     const T a = (T)S->c1[0];
     const T b = (T)(i > 0 ? S->beta[i - 1] : 0.0);
@@ -157,8 +191,9 @@ recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosS
 #pragma unroll
         for (int u = 0; u < kGroup; ++u) {
             if (j0 + u < m) {
-                const double val = (sizeof(T) == 4) ? (double)hi[u] + (double)lo[u] : acc[u];
-                const double s = block_sum(val, sh);
+                double s;
+                if constexpr (sizeof(T) == 4) s = block_sum_ff(hi[u], lo[u], reinterpret_cast<float *>(sh));
+                else s = block_sum(acc[u], sh);
                 if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
             }
         }
@@ -232,7 +267,7 @@ update_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const double 
         ff_add_prod(hi, lo, v, v);
     }
     if (part) {
-        const double s = block_sum((double)hi + (double)lo, sh);
+        const double s = block_sum_ff(hi, lo, reinterpret_cast<float *>(sh));
         if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
     }
 }
@@ -283,38 +318,47 @@ __global__ void cycle_reset_kernel(LanczosScalars *S)
 }
 
 // ---- symmetric tridiagonal eigenproblem (one warp) --------------------------
-// Number of eigenvalues below x (Sturm sequence of the LDL^T pivots of T - xI).
-__device__ int sturm_count(const double *a, const double *b2, int m, double x, double tiny)
+// Number of eigenvalues below x: sign changes of the characteristic-polynomial
+// sequence p_0 = 1, p_1 = a_0 - x, p_i = (a_{i-1} - x) p_{i-1} - b2_{i-2} p_{i-2}
+// (Sturm), evaluated without divisions on a matrix scaled to entries <= 1 so that
+// no p_i leaves the double range for m <= 64.  A zero p_i takes the sign opposite
+// to p_{i-1}.
+template <typename R>
+__device__ __forceinline__ int sturm_count(const R *a, const R *b2, int m, R x)
 {
-    int cnt = 0;
-    double d = 1.0;
-    for (int i = 0; i < m; ++i) {
-        d = a[i] - x - (i > 0 ? b2[i - 1] / d : 0.0);
-        if (d == 0.0) d = -tiny;
-        if (d < 0.0) ++cnt;
+    R pm2 = R(1), pm1 = a[0] - x;
+    if (pm1 == R(0)) pm1 = -R(1e-30);
+    int cnt = pm1 < R(0);
+    for (int i = 1; i < m; ++i) {
+        R p = (a[i] - x) * pm1 - b2[i - 1] * pm2;
+        if (p == R(0)) p = pm1 < R(0) ? R(1e-30) : -R(1e-30);
+        cnt += (p < R(0)) != (pm1 < R(0));
+        pm2 = pm1;
+        pm1 = p;
     }
     return cnt;
 }
 
-// j-th smallest eigenvalue (j = 1, 2, ...) by 33-way multisection across the warp
-__device__ double kth_eigenvalue(const double *a, const double *b2, int m, int j, double lo, double hi,
-                                 double tiny)
+// j-th smallest eigenvalue (j = 1, 2, ...) inside [lo, hi] by 33-way multisection
+// across the warp, until the bracket is `rel` wide (relative) or stops shrinking
+template <typename R>
+__device__ void multisect(const R *a, const R *b2, int m, int j, R &lo, R &hi, R rel)
 {
     const int lane = threadIdx.x & 31;
     for (int it = 0; it < 64; ++it) {
-        const double w = hi - lo;
-        if (w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) || w <= tiny) break;
-        const double xl = lo + w * (double)(lane + 1) / 33.0;
-        const int c = sturm_count(a, b2, m, xl, tiny);
+        const R w = hi - lo;
+        const R mag = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
+        if (w <= rel * mag || w <= R(1e-300)) break;
+        const R xl = lo + w * R(lane + 1) / R(33);
+        const int c = sturm_count<R>(a, b2, m, xl);
         const unsigned below = __ballot_sync(0xffffffffu, c < j);    // eigenvalue j lies above xl
         const int nb = __popc(below);                                 // the points below are a prefix
-        const double new_lo = nb > 0 ? __shfl_sync(0xffffffffu, xl, nb - 1) : lo;
-        const double new_hi = nb < 32 ? __shfl_sync(0xffffffffu, xl, nb < 32 ? nb : 31) : hi;
+        const R new_lo = nb > 0 ? __shfl_sync(0xffffffffu, xl, nb - 1) : lo;
+        const R new_hi = nb < 32 ? __shfl_sync(0xffffffffu, xl, nb < 32 ? nb : 31) : hi;
         if (new_lo == lo && new_hi == hi) break;
         lo = new_lo;
         hi = new_hi;
     }
-    return 0.5 * (lo + hi);
 }
 
 // Solve (T - theta I) z = r for a symmetric tridiagonal T by Gaussian
@@ -360,45 +404,59 @@ __device__ void tridiag_warp(const double *alpha, const double *beta, int m, dou
                              double *a, double *b, double *b2, double *z, double *u0, double *u1, double *u2)
 {
     const int lane = threadIdx.x & 31;
+    // Gershgorin scale of T (each lane computes it; m <= 64)
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double rad = (i + 1 < m ? fabs(beta[i]) : 0.0) + (i > 0 ? fabs(beta[i - 1]) : 0.0);
+        scale = fmax(scale, fabs(alpha[i]) + rad);
+    }
+    if (!(scale > 0.0)) scale = 1.0;
+    const double inv = 1.0 / scale;
+    // scaled copies: a, b, b2 (double) and their FP32 twins in u0/u1 storage
+    float *af = reinterpret_cast<float *>(u0);
+    float *b2f = reinterpret_cast<float *>(u1);
     for (int i = lane; i < m; i += 32) {
-        a[i] = alpha[i];
-        b[i] = (i + 1 < m) ? beta[i] : 0.0;
+        a[i] = alpha[i] * inv;
+        b[i] = (i + 1 < m) ? beta[i] * inv : 0.0;
         b2[i] = b[i] * b[i];
+        af[i] = (float)a[i];
+        b2f[i] = (float)b2[i];
     }
     __syncwarp();
     if (m == 1) {
-        if (lane == 0) { theta_out[0] = a[0]; theta_out[1] = INFINITY; s_out[0] = 1.0; }
+        if (lane == 0) { theta_out[0] = alpha[0]; theta_out[1] = INFINITY; s_out[0] = 1.0; }
         __syncwarp();
         return;
     }
-    // Gershgorin interval and the scale of T
-    double lo = INFINITY, hi = -INFINITY, scale = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const double rad = fabs(b[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0);
-        lo = fmin(lo, a[i] - rad);
-        hi = fmax(hi, a[i] + rad);
-        scale = fmax(scale, fabs(a[i]) + rad);
-    }
-    const double tiny = fmax(scale, DBL_MIN) * DBL_EPSILON;
-    lo -= tiny; hi += tiny;
-    const double t1 = kth_eigenvalue(a, b2, m, 1, lo, hi, DBL_MIN);
-    const double t2 = kth_eigenvalue(a, b2, m, 2, lo, hi, DBL_MIN);
+    // FP32 brackets of the two lowest eigenvalues (entries are within [-1, 1])
+    float lo1 = -1.25f, hi1 = 1.25f, lo2 = -1.25f, hi2 = 1.25f;
+    multisect<float>(af, b2f, m, 1, lo1, hi1, 4e-7f);
+    multisect<float>(af, b2f, m, 2, lo2, hi2, 4e-7f);
+    // FP64 refinement of the lowest from its (slightly widened) FP32 bracket
+    double lo = (double)lo1 - 1e-6, hi = (double)hi1 + 1e-6;
+    if (sturm_count<double>(a, b2, m, lo) >= 1) lo = -1.25;      // the widened bracket must hold it
+    if (sturm_count<double>(a, b2, m, hi) < 1) hi = 1.25;
+    multisect<double>(a, b2, m, 1, lo, hi, 2.0 * DBL_EPSILON);
+    const double t1 = 0.5 * (lo + hi);
+    const double t2 = 0.5 * ((double)lo2 + (double)hi2);
+    __syncwarp();
     if (lane == 0) {
-        // inverse iteration for the eigenvector of t1
+        // inverse iteration for the eigenvector of t1 (scaled matrix)
+        const double tiny = DBL_EPSILON;
         for (int i = 0; i < m; ++i) z[i] = 1.0;
-        for (int it = 0; it < 3; ++it) {
+        for (int it = 0; it < 2; ++it) {
             tridiag_solve(a, b, m, t1, z, u0, u1, u2, tiny);
             double nrm = 0.0;
             for (int i = 0; i < m; ++i) nrm += z[i] * z[i];
-            nrm = sqrt(nrm);
-            for (int i = 0; i < m; ++i) z[i] /= nrm;
+            nrm = 1.0 / sqrt(nrm);
+            for (int i = 0; i < m; ++i) z[i] *= nrm;
         }
         double big = 0.0; int ib = 0;                 // fix the sign: largest component positive
         for (int i = 0; i < m; ++i) if (fabs(z[i]) > big) { big = fabs(z[i]); ib = i; }
         const double sg = z[ib] < 0.0 ? -1.0 : 1.0;
         for (int i = 0; i < m; ++i) s_out[i] = sg * z[i];
-        theta_out[0] = t1;
-        theta_out[1] = t2;
+        theta_out[0] = t1 * scale;
+        theta_out[1] = t2 * scale;
     }
     __syncwarp();
 }
@@ -453,7 +511,7 @@ ritz_f32_kernel(float *__restrict__ Q, int64_t ldq, const int *__restrict__ m_de
         Q[i] = v;
         ff_add_prod(hi, lo, v, v);
     }
-    const double sum = block_sum((double)hi + (double)lo, sh);
+    const double sum = block_sum_ff(hi, lo, reinterpret_cast<float *>(sh));
     if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = sum;
 }
 
@@ -515,6 +573,12 @@ struct DotAcc<float> {                // float-float (exact products, TwoSum)
     __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
+__device__ __forceinline__ double block_reduce(const DotAcc<double> &a, double *sh) { return block_sum(a.get(), sh); }
+__device__ __forceinline__ double block_reduce(const DotAcc<float> &a, double *sh)
+{
+    return block_sum_ff(a.hi, a.lo, reinterpret_cast<float *>(sh));
+}
+
 template <typename T>
 __device__ __forceinline__ T fma_t(T a, T b, T c);
 template <>
@@ -544,7 +608,7 @@ seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, c
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
                 if (j0 + u < m) {
-                    const double sum = block_sum(acc[u].get(), sh);
+                    const double sum = block_reduce(acc[u], sh);
                     if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
                 }
             }
@@ -600,7 +664,7 @@ seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq,
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
                 if (j0 + u < m) {
-                    const double sum = block_sum(acc[u].get(), sh);
+                    const double sum = block_reduce(acc[u], sh);
                     if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
                 }
             }
@@ -630,7 +694,7 @@ seg_update_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m,
             v[e0 + e] = x;
             nrm.add(x, x);
         }
-        const double sum = block_sum(nrm.get(), sh);
+        const double sum = block_reduce(nrm, sh);
         if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
     }
 }
@@ -674,7 +738,7 @@ seg_ritz_kernel(const BatchVec V, T *__restrict__ Q, int64_t ldq, const BatchSta
             Q[e0 + e] = x;
             nrm.add(x, x);
         }
-        const double sum = block_sum(nrm.get(), sh);
+        const double sum = block_reduce(nrm, sh);
         if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
     }
 }
