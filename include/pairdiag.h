@@ -268,6 +268,31 @@ int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs,
                                 pairdiag_mlp_t *mlp, double *e0, int *status,
                                 pairdiag_batch_result *results, void *stream);
 
+/* --------------------------------------------------------- autotuner ---- */
+/*
+ * H*x schedule autotuner (an addition of this library; the paper has a single
+ * CPU code path).  For one problem and precision it times the H*x kernel for
+ * every block split L = low_bits in [min(omega,8), min(omega,13)] and both
+ * kernel variants (median of `reps` launches on a random vector, CUDA events)
+ * and records the fastest (low_bits, hx_variant) for (omega, n_pairs,
+ * precision) in a process-wide table.  pairdiag_create and the batched solver
+ * use a recorded schedule when opt.low_bits and opt.hx_variant are 0.
+ *   best: host, receives the fastest; all: host [*n_all] (nullable), receives every
+ *   timed candidate, *n_all = capacity on entry, count on return.  Synchronous;
+ *   allocates and frees its own vectors and handles.
+ */
+typedef struct {
+    int    low_bits;
+    int    hx_variant;
+    double ms;              /* median H*x duration */
+} pairdiag_tune_entry;
+
+int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, int precision, int reps,
+                      pairdiag_tune_entry *best, pairdiag_tune_entry *all, int *n_all);
+/* Record (low_bits > 0) or clear (low_bits == 0) a schedule / read it (0, 0 if none). */
+int pairdiag_tune_set(int omega, int n_pairs, int precision, int low_bits, int hx_variant);
+int pairdiag_tune_get(int omega, int n_pairs, int precision, int *low_bits, int *hx_variant);
+
 /* ------------------------------------------------------- diagnostics ---- */
 
 /* Number of CUDA kernels this library has launched since it was loaded (all

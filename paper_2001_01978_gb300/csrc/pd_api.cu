@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -27,6 +28,27 @@ std::atomic<long long> g_kernel_launches{0};
 
 namespace {
 thread_local std::string g_last_error = "no error";
+
+// autotuned H*x schedules: (omega, n, precision) -> (low_bits, hx_variant)
+struct TuneKey {
+    int omega, n, precision;
+    bool operator<(const TuneKey &o) const
+    {
+        return omega != o.omega ? omega < o.omega : n != o.n ? n < o.n : precision < o.precision;
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+bool tuned_schedule(int omega, int n, int precision, int *low_bits, int *variant)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(TuneKey{omega, n, precision});
+    if (it == g_tune.end()) return false;
+    *low_bits = it->second.first;
+    *variant = it->second.second;
+    return true;
+}
 }
 
 namespace pd {
@@ -592,6 +614,10 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     if (o.hx_variant < 0 || o.hx_variant > 2) return fail(PD_EINVAL, "hx_variant outside 0..2");
     if (o.start < PD_START_RANDOM || o.start > PD_START_MLP) return fail(PD_EINVAL, "bad start kind");
 
+    if (o.low_bits == 0 && o.hx_variant == 0) {   // an autotuned schedule, if one was recorded
+        int lb = 0, hv = 0;
+        if (tuned_schedule(omega, n_pairs, o.precision, &lb, &hv)) { o.low_bits = lb; o.hx_variant = hv; }
+    }
     pairdiag *h = new pairdiag();
     h->omega = omega; h->n = n_pairs; h->opt = o;
     h->e.assign(e, e + omega);
@@ -814,6 +840,95 @@ int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const dou
     PD_CUDA(cudaMemcpyAsync(theta, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaMemcpyAsync(s, S->s, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------
+int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, int precision, int reps,
+                      pairdiag_tune_entry *best, pairdiag_tune_entry *all, int *n_all)
+{
+    if (!e || !G || !best || reps < 1) return fail(PD_EINVAL, "bad argument");
+    if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED) return fail(PD_EINVAL, "bad precision");
+    if (omega < 1 || omega > kMaxOmega || n_pairs < 0 || n_pairs > omega) return fail(PD_EINVAL, "bad size");
+    const int lmax = std::min(omega, kMaxLow), lmin = std::max(1, std::min(omega, 8));
+    std::vector<pairdiag_tune_entry> res;
+    const size_t es = precision == PD_PREC_FP64 ? 8 : 4;
+    const int64_t dim = (int64_t)host_binom(omega, n_pairs);
+    void *x = nullptr, *y = nullptr;
+    PD_CUDA(cudaMalloc(&x, es * (size_t)dim));
+    cudaError_t ce = cudaMalloc(&y, es * (size_t)dim);
+    if (ce != cudaSuccess) { cudaFree(x); PD_CUDA(ce); }
+    int rc = PD_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int L = lmin; L <= lmax && rc == PD_OK; ++L) {
+        for (int variant = 1; variant <= 2 && rc == PD_OK; ++variant) {
+            pairdiag_options o;
+            pairdiag_default_options(&o);
+            o.low_bits = L;
+            o.hx_variant = variant;
+            o.precision = precision;
+            pairdiag_t *h = nullptr;
+            if ((rc = pairdiag_create(omega, n_pairs, e, G, &o, &h)) != PD_OK) break;
+            if (variant == 2 && hx_variant(h->B, precision == PD_PREC_FP64 ? 0 : 1) != 2) {
+                pairdiag_destroy(h);             // variant 2 does not fit: same as variant 1
+                continue;
+            }
+            rc = [&]() -> int {
+                PD_CUDA(random_start_launch(precision == PD_PREC_FP64 ? 0 : 1, x, dim, 7, h->st));
+                for (int w = 0; w < 2; ++w) PD_TRY(hx(h, precision == PD_PREC_FP64 ? 0 : 1, x, y));
+                std::vector<float> t(reps);
+                for (int r = 0; r < reps; ++r) {
+                    PD_CUDA(cudaEventRecord(e0, h->st));
+                    PD_TRY(hx(h, precision == PD_PREC_FP64 ? 0 : 1, x, y));
+                    PD_CUDA(cudaEventRecord(e1, h->st));
+                    PD_CUDA(cudaEventSynchronize(e1));
+                    PD_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+                }
+                std::sort(t.begin(), t.end());
+                res.push_back(pairdiag_tune_entry{L, variant, (double)t[reps / 2]});
+                return PD_OK;
+            }();
+            pairdiag_destroy(h);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    if (rc != PD_OK) return rc;
+    if (res.empty()) return fail(PD_ECUDA, "autotune: no candidate ran");
+    const auto it = std::min_element(res.begin(), res.end(),
+                                     [](const pairdiag_tune_entry &a, const pairdiag_tune_entry &b) { return a.ms < b.ms; });
+    *best = *it;
+    if (all && n_all) {
+        const int cap = *n_all;
+        int k = 0;
+        for (const auto &r : res)
+            if (k < cap) all[k++] = r;
+        *n_all = k;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[TuneKey{omega, n_pairs, precision}] = {best->low_bits, best->hx_variant};
+    }
+    return PD_OK;
+}
+
+int pairdiag_tune_set(int omega, int n_pairs, int precision, int low_bits, int hx_variant_)
+{
+    if (low_bits < 0 || low_bits > kMaxLow || hx_variant_ < 0 || hx_variant_ > 2) return fail(PD_EINVAL, "bad schedule");
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (low_bits == 0) g_tune.erase(TuneKey{omega, n_pairs, precision});
+    else g_tune[TuneKey{omega, n_pairs, precision}] = {low_bits, hx_variant_};
+    return PD_OK;
+}
+
+int pairdiag_tune_get(int omega, int n_pairs, int precision, int *low_bits, int *hx_variant_)
+{
+    if (!low_bits || !hx_variant_) return fail(PD_EINVAL, "null argument");
+    if (!tuned_schedule(omega, n_pairs, precision, low_bits, hx_variant_)) { *low_bits = 0; *hx_variant_ = 0; }
     return PD_OK;
 }
 

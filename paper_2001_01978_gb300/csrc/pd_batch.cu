@@ -112,6 +112,10 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
             }
         }
         int L = opt.low_bits > 0 ? opt.low_bits : 12;
+        if (opt.low_bits == 0) {                  // an autotuned block split for this (omega, N)
+            int lb = 0, hv = 0;
+            if (pairdiag_tune_get(om, n, opt.precision, &lb, &hv) == PD_OK && lb > 0) L = lb;
+        }
         L = std::min(L, std::min(om, kMaxLow));
         const int H = om - L;
         if (!tab_of_L.count(L)) {

@@ -40,6 +40,10 @@ class pairdiag_batch_result(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 
+class pairdiag_tune_entry(ctypes.Structure):
+    _fields_ = [("low_bits", ctypes.c_int), ("hx_variant", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
 class PairDiagError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (status {code})")
@@ -90,6 +94,10 @@ _SIGNATURES = {
     "pairdiag_set_start_weights": (ctypes.c_int, [_H, _P]),
     "pairdiag_product_fit": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_product_start_dev": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(pairdiag_tune_entry), _P, _P]),
+    "pairdiag_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pairdiag_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     "pairdiag_multidot_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P,
                                                  ctypes.c_int64, _P, _P]),
 }
@@ -397,6 +405,31 @@ def pairdiag_product_start_dev(h, w, v) -> None:
     import torch
     w = np.ascontiguousarray(w, dtype=np.float64)
     _check(lib().pairdiag_product_start_dev(h, _np_ptr(w), _dev_ptr(v, torch.float64)))
+
+
+# ---------------------------------------------------------------- autotuner ---
+def pairdiag_autotune(omega: int, n_pairs: int, e, G, precision: int = PD_PREC_MIXED, reps: int = 5):
+    """Time every (low_bits, hx_variant) candidate; returns (best, all) as dicts."""
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    best = pairdiag_tune_entry()
+    cap = 16
+    arr = (pairdiag_tune_entry * cap)()
+    n = ctypes.c_int(cap)
+    _check(lib().pairdiag_autotune(omega, n_pairs, _np_ptr(e), _np_ptr(G), precision, reps, ctypes.byref(best),
+                                   ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(n)))
+    as_d = lambda t: {"low_bits": t.low_bits, "hx_variant": t.hx_variant, "ms": t.ms}
+    return as_d(best), [as_d(arr[i]) for i in range(n.value)]
+
+
+def pairdiag_tune_set(omega: int, n_pairs: int, precision: int, low_bits: int, hx_variant: int = 1) -> None:
+    _check(lib().pairdiag_tune_set(omega, n_pairs, precision, low_bits, hx_variant))
+
+
+def pairdiag_tune_get(omega: int, n_pairs: int, precision: int):
+    lb, hv = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pairdiag_tune_get(omega, n_pairs, precision, ctypes.byref(lb), ctypes.byref(hv)))
+    return lb.value, hv.value
 
 
 # ------------------------------------------------------------ convenience ---

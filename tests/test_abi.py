@@ -59,3 +59,14 @@ def test_no_cpu_fallback_in_product_path():
     for f in pkg.rglob("*.py"):
         src = f.read_text()
         assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_tune_table_host_only(libpath):
+    import paper_2001_01978_gb300 as pd
+    assert pd.pairdiag_tune_get(20, 10, 1) == (0, 0)
+    pd.pairdiag_tune_set(20, 10, 1, 11, 2)
+    assert pd.pairdiag_tune_get(20, 10, 1) == (11, 2)
+    pd.pairdiag_tune_set(20, 10, 1, 0, 0)
+    assert pd.pairdiag_tune_get(20, 10, 1) == (0, 0)
+    with pytest.raises(pd.PairDiagError):
+        pd.pairdiag_tune_set(20, 10, 1, 14, 1)

@@ -267,3 +267,20 @@ def test_tridiag_clustered():
     w = np.linalg.eigvalsh(T)
     assert abs(theta[0] - w[0]) < 1e-14 and abs(theta[1] - w[1]) < 1e-5
     assert np.linalg.norm(T @ svec - theta[0] * svec) < 1e-12
+
+
+# ---------------------------------------------------------------- autotuner ---
+def test_autotune_records_fastest_schedule():
+    omega, n = 18, 8
+    e, G = pd_inputs.separable_noise(omega, seed=17)
+    best, allc = pd.pairdiag_autotune(omega, n, e, G, pd.PD_PREC_MIXED, reps=3)
+    assert allc and best["ms"] == min(c["ms"] for c in allc)
+    assert {c["low_bits"] for c in allc} == set(range(8, 14))
+    assert pd.pairdiag_tune_get(omega, n, pd.PD_PREC_MIXED) == (best["low_bits"], best["hx_variant"])
+    # a handle created afterwards uses the recorded schedule and stays exact
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED) as s:
+        x = pd_inputs.random_vector(s.dim, 5)
+        y = pd.pairdiag_hx(s.h, x)
+    assert np.max(np.abs(y - oracle.hx(omega, n, e, G, x))) <= 1e-11 * np.max(np.abs(y))
+    pd.pairdiag_tune_set(omega, n, pd.PD_PREC_MIXED, 0, 0)
+    assert pd.pairdiag_tune_get(omega, n, pd.PD_PREC_MIXED) == (0, 0)
