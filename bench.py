@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--warm", action="store_true",
                     help="Omega=30 workload: FP64 random start vs mixed + learned warm start (own JSON line)")
     ap.add_argument("--train-problems", type=int, default=240)
+    ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--no-mlp", action="store_true", help="batch mode without the learned warm start")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip tuning the H*x schedule of the workload before the timed solves")
@@ -138,16 +139,16 @@ def hx_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, precision: str):
-    """DRAM bytes per H*x launch from the committed ncu summary, or None when the
-    kernel source changed since the capture."""
+def ncu_traffic(workload: str, precision: str, low_bits: int, variant: int):
+    """DRAM bytes per H*x launch of this schedule from the committed ncu summary,
+    or None when there is none or the kernel source changed since the capture."""
     f = ROOT / "profiles" / "hx_traffic.txt"
     if not f.exists():
         return None
     for line in f.read_text().splitlines():
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == workload and parts[1] == precision:
-            return float(parts[2]) if parts[3] == hx_source_hash() else None
+        if len(parts) >= 6 and not line.startswith("#") and parts[:4] == [workload, precision, str(low_bits), str(variant)]:
+            return float(parts[4]) if parts[5] == hx_source_hash() else None
     return None
 
 
@@ -256,12 +257,12 @@ def run_ours(args):
             tuned[pname] = {"best": best, "candidates": cands}
     # the chosen form: mixed precision from the learned warm start (trained once,
     # outside the timed region, on ground states the solver computes at Omega <= 18)
-    ws, train_s, l0, l1, trows = (None, None, None, None, None) if args.no_mlp else train_warm_start(args.train_problems)
+    ws, train_s, l0, l1, trows = (None, None, None, None, None) if args.no_mlp else train_warm_start(args.train_problems, args.train_steps)
     mixed = make(pd.PD_PREC_MIXED)
     if ws is not None:
         mixed.close()
         mixed = pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=args.window,
-                          start=pd.PD_START_MLP, seed=1)
+                          start=pd.PD_START_MLP, seed=1, hx_variant=args.hx_variant, low_bits=args.low_bits)
         pd.pairdiag_set_stream(mixed.h, stream)
         ws.attach(mixed.h)
     mixed_rand = None if ws is None else make(pd.PD_PREC_MIXED)
@@ -343,7 +344,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=args.window, seed=1,
-                       start=pd.PD_START_MLP if ws is not None else pd.PD_START_RANDOM) as s:
+                       start=pd.PD_START_MLP if ws is not None else pd.PD_START_RANDOM,
+                       hx_variant=args.hx_variant, low_bits=args.low_bits) as s:
             if ws is not None:
                 ws.attach(s.h)
             r = s.ground_state(args.tol, want_vector=True)      # E0 + eigenvector into host memory
@@ -368,8 +370,11 @@ def run_ours(args):
     alg_bytes = nnz * 4 + 2 * dim * 4
     avg_hx_s = (hx_ms / hx_count) * 1e-3
     achieved = alg_bytes / avg_hx_s / 1e9
-    traffic = ncu_traffic(args.workload, "fp32")
-    roofline = {"kernel": "hx_kernel<float,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+    lb, hv = pd.pairdiag_tune_get(omega, n, pd.PD_PREC_MIXED)
+    if args.low_bits:
+        lb, hv = args.low_bits, args.hx_variant or 1
+    traffic = ncu_traffic(args.workload, "fp32", lb or 12, hv or 1)
+    roofline = {"kernel": "H*x FP32 (low_bits %d, variant %d)" % (lb or 12, hv or 1), "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_hx_s * 1e3,
                 "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": hx_ms / total_ms}
@@ -472,14 +477,14 @@ def run_hx_only(args):
     return 0
 
 
-def train_warm_start(count: int):
+def train_warm_start(count: int, steps: int = 2500):
     """One-off: train the warm-start network on ground states the solver computes
     at Omega <= 18 (returns the network and the seconds it took)."""
     from paper_2001_01978_gb300 import warmstart
     t0 = time.perf_counter()
     X, T = warmstart.training_set(pd_inputs.training_problems(count, seed=11, omega_lo=10, omega_hi=18))
     ws = warmstart.WarmStart(seed=0)
-    hist = ws.train(X, T, steps=2500, lr=2e-3)
+    hist = ws.train(X, T, steps=steps, lr=2e-3)
     return ws, time.perf_counter() - t0, float(hist[0]), float(hist[-1]), len(X)
 
 
@@ -490,7 +495,7 @@ def run_warm(args):
     import torch
     import paper_2001_01978_gb300 as pd
     torch.cuda.set_device(0)
-    ws, train_s, l0, l1, rows = train_warm_start(args.train_problems)
+    ws, train_s, l0, l1, rows = train_warm_start(args.train_problems, args.train_steps)
     omega, n, e, G = pd_inputs.workload("omega30_n15_sepnoise_s2")
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -539,7 +544,7 @@ def run_batch(args):
     nnz = sum(d * n * (om - n) for d, (om, n, _, _) in zip(dims, probs))
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    ws, train_s = (None, None) if args.no_mlp else train_warm_start(args.train_problems)[:2]
+    ws, train_s = (None, None) if args.no_mlp else train_warm_start(args.train_problems, args.train_steps)[:2]
     forms = [("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM), ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)]
     if ws is not None:
         forms.insert(0, ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP))
