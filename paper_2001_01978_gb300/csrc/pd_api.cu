@@ -7,7 +7,7 @@
 // from the ground Ritz vector (Sec. 3.4).  Convergence is the paper's
 // |beta_1/alpha_1| <= tol measured at the first step of each cycle (Sec. 5.1).
 #include "pd_internal.h"
-#include "../../include/pairdiag.h"
+#include "pairdiag.h"
 
 #include <algorithm>
 #include <chrono>

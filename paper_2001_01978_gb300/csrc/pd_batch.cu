@@ -12,7 +12,7 @@
 // are captured once into a CUDA graph and replayed; the host synchronises once
 // per cycle to count the problems still running.
 #include "pd_internal.h"
-#include "../../include/pairdiag.h"
+#include "pairdiag.h"
 
 #include <algorithm>
 #include <cmath>

@@ -49,26 +49,12 @@ __host__ __device__ inline Layout layout(int omega, int L, int H, int max_block,
     s.d = off;    off = align16(off + sizeof(A) * omega);
     s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
     s.x = off;    off = align16(off + sizeof(T) * max_block);
-    s.xn = off;   off = align16(off + sizeof(T) * 3 * (size_t)max_block);   // ring of 3 staging buffers
+    s.xn = off;   off = align16(off + sizeof(T) * max_block);
     s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
     s.mx = off;   off = align16(off + sizeof(uint64_t) * (H > 0 ? H : 1));
     s.total = off;
     return s;
 }
-
-// asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes)
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // position of the n-th (0-based) set bit of w
 __device__ __forceinline__ int nth_set_bit(uint64_t w, int n)
@@ -103,7 +89,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
                                          const uint64_t *__restrict__ binom,
                                          const A *sG, const A *sd, const uint16_t *sRank, T *sx, T *sxn,
                                          HHop<A> *sHH, uint64_t *sMX, const T *__restrict__ x,
-                                         T *__restrict__ y, const int MB)
+                                         T *__restrict__ y)
 {
     const int tid = threadIdx.x;
     const uint32_t maskL = (1u << L) - 1u;
@@ -133,28 +119,6 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
     }
     for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
     __syncthreads();
-
-    // neighbouring blocks of the high<->low hops: fetched two stages ahead by
-    // cp.async into a ring of three buffers, overlapping the copies with compute
-    auto next_stage = [&](int t) {
-        ++t;
-        while (t < H && sMX[t] == ~0ull) ++t;
-        return t;
-    };
-    auto issue = [&](int t, int slot) {
-        if (t < H) {
-            const bool occ_t = (h >> t) & 1ull;
-            const int n2 = (int)__ldg(binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
-            const T *src = x + sMX[t];
-            T *dst = sxn + slot * MB;
-            for (int r = tid; r < n2; r += kThreads) cp_async_elem(dst + r, src + r);
-        }
-        cp_async_commit();                        // possibly empty: keeps the group count uniform
-    };
-    const int st0 = next_stage(-1);
-    const int st1 = st0 < H ? next_stage(st0) : H;
-    issue(st0, 0);
-    issue(st1, 1);
 
     A Dh = A(0);
     for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
@@ -210,17 +174,18 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         }
     }
 
-    // high <-> low: consume the staged blocks in order
-    int slot = 0, tn = st1;
-    for (int t = st0; t < H;) {
-        const int tnn = tn < H ? next_stage(tn) : H;
-        cp_async_wait<1>();                       // stage t landed (stage tn may be in flight)
-        __syncthreads();                          // visible to all; previous stage fully consumed
-        issue(tnn, slot == 0 ? 2 : slot - 1);     // the buffer of the previous stage is free
-        const T *xs = sxn + slot * MB;
+    // high <-> low: stage each neighbouring block once (plain loads between two
+    // barriers; measured faster on GB300 than a cp.async ring fetching ahead)
+    for (int t = 0; t < H; ++t) {
+        const uint64_t b2 = sMX[t];
+        if (b2 == ~0ull) continue;            // CTA-uniform
         const bool occ_t = (h >> t) & 1ull;
+        const int n2 = (int)__ldg(binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
+        __syncthreads();
+        for (int r = tid; r < n2; r += kThreads) sxn[r] = x[b2 + r];
+        __syncthreads();
         const int go = L + t;
-        if (occ_t) {                               // pair: high orbit go -> empty low orbit q
+        if (occ_t) {                           // pair: high orbit go -> empty low orbit q
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 if (tid + i * kThreads < nk) {
@@ -230,12 +195,12 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
                     for (int v = 0; v < L - k; ++v) {
                         const int q = __ffs(emp) - 1;
                         emp &= emp - 1;
-                        a += sG[q * omega + go] * A(xs[sRank[l | (1u << q)]]);
+                        a += sG[q * omega + go] * A(sxn[sRank[l | (1u << q)]]);
                     }
                     acc[i] = a;
                 }
             }
-        } else {                                   // pair: occupied low orbit o -> high orbit go
+        } else {                               // pair: occupied low orbit o -> high orbit go
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 if (tid + i * kThreads < nk) {
@@ -245,17 +210,13 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
                     for (int u = 0; u < k; ++u) {
                         const int o = __ffs(occ) - 1;
                         occ &= occ - 1;
-                        a += sG[go * omega + o] * A(xs[sRank[l ^ (1u << o)]]);
+                        a += sG[go * omega + o] * A(sxn[sRank[l ^ (1u << o)]]);
                     }
                     acc[i] = a;
                 }
             }
         }
-        slot = slot == 2 ? 0 : slot + 1;
-        t = tn;
-        tn = tnn;
     }
-    cp_async_wait<0>();
 
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -296,7 +257,7 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
         if (b >= B.nblocks) break;
 
         hx_block<T, A, R>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
-                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y, B.max_block);
+                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y);
     }
 }
 
@@ -346,7 +307,7 @@ hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__res
         }
         hx_block<T, A, R>(dsc.omega, dsc.L, dsc.omega - dsc.L, dsc.n, __ldg(BB.blk_h + b), __ldg(BB.blk_base + b),
                           BB.lowword_all + dsc.tab_off, BB.binom, sG, sd, sRank, sx, sxn, sHH, sMX,
-                          x + dsc.vec_off, y + dsc.vec_off, BB.max_block);
+                          x + dsc.vec_off, y + dsc.vec_off);
     }
 }
 

@@ -19,7 +19,6 @@ constexpr int kGroup = 8;             // vectors handled per pass of a multi-dot
 constexpr int kGrid = 152 * 4;
 
 __device__ __forceinline__ double ld(const double *p, int64_t i) { return __ldg(p + i); }
-__device__ __forceinline__ double ld(const float *p, int64_t i) { return (double)__ldg(p + i); }
 
 // block-wide sum of one double per thread; result valid in thread 0
 __device__ __forceinline__ double block_sum(double v, double *sh)
@@ -348,7 +347,7 @@ __device__ void multisect(const R *a, const R *b2, int m, int j, R &lo, R &hi, R
     for (int it = 0; it < 64; ++it) {
         const R w = hi - lo;
         const R mag = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
-        if (w <= rel * mag || w <= R(1e-300)) break;
+        if (w <= rel * mag || w <= (sizeof(R) == 4 ? R(FLT_MIN) : R(DBL_MIN))) break;
         const R xl = lo + w * R(lane + 1) / R(33);
         const int c = sturm_count<R>(a, b2, m, xl);
         const unsigned below = __ballot_sync(0xffffffffu, c < j);    // eigenvalue j lies above xl

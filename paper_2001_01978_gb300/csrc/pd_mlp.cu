@@ -12,7 +12,7 @@
 // Adam.  Sizes are tiny (rows = orbits of the training problems), so one tiled
 // kernel serves every product of the forward and backward passes.
 #include "pd_internal.h"
-#include "../../include/pairdiag.h"
+#include "pairdiag.h"
 
 #include <cuda_bf16.h>
 
