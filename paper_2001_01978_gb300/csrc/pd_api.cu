@@ -120,7 +120,8 @@ struct pairdiag {
     uint16_t *d_lowword = nullptr, *d_rankL = nullptr;
     double *d_G64 = nullptr, *d_d64 = nullptr;
     float *d_G32 = nullptr, *d_d32 = nullptr;
-    int *d_counter = nullptr;
+    Tickets *d_tk = nullptr;         // counters of the persistent and streaming kernels
+    double *d_blkdot = nullptr;      // [nblocks] per-block partial sums of the fused alpha
     double *d_part = nullptr;        // partial sums of the streaming kernels
     size_t part_count = 0;
     LanczosScalars *d_S = nullptr;
@@ -129,6 +130,7 @@ struct pairdiag {
     int rgrid = 0;                   // grid of the per-row reductions
     // Lanczos window (lazily allocated) per storage type
     void *d_Q[2] = {nullptr, nullptr};
+    int64_t ldq = 0;                 // stride between window vectors: dim rounded up to 4 elements
     int Qwin[2] = {0, 0};
     void *d_p[2] = {nullptr, nullptr};
     double *d_v64 = nullptr, *d_w64 = nullptr;
@@ -152,7 +154,7 @@ void free_all(pairdiag *h)
     }
     h->hx_events.clear();
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
-                    h->d_d64, h->d_G32, h->d_d32, h->d_counter, h->d_part, h->d_S, h->d_small,
+                    h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -250,7 +252,7 @@ int ensure_window(pairdiag *h, int dtype, int window)
     if (h->d_Q[dtype] && h->Qwin[dtype] >= window) return PD_OK;
     if (h->d_Q[dtype]) { cudaFree(h->d_Q[dtype]); h->d_Q[dtype] = nullptr; }
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, es * (size_t)window * (size_t)h->dim);
+    cudaError_t e = cudaMalloc(&q, es * (size_t)window * (size_t)h->ldq);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(PD_ENOMEM, "Lanczos window of %d x %lld elements: %s", window, (long long)h->dim,
@@ -272,7 +274,8 @@ int ensure_fp64_pair(pairdiag *h)
     return PD_OK;
 }
 
-int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nullptr)
+// y = H x; with dot_out also x^T y -> *dot_out (fused into the same launch)
+int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nullptr, double *dot_out = nullptr)
 {
     HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
     std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
@@ -288,7 +291,9 @@ int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nul
         ev = &h->hx_events[h->hx_events_used++];
         PD_CUDA(cudaEventRecord(ev->first, h->st));
     }
-    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_counter, h->hxgrid[precision], h->st, skip));
+    const HxDot dot{h->d_blkdot, dot_out};
+    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_tk, h->hxgrid[precision], h->st, skip,
+                      dot_out ? &dot : nullptr));
     if (ev) PD_CUDA(cudaEventRecord(ev->second, h->st));
     return PD_OK;
 }
@@ -299,7 +304,7 @@ T *vec(void *base, int64_t i, int64_t dim) { return static_cast<T *>(base) + i *
 void *qvec(pairdiag *h, int dtype, int i)
 {
     const size_t es = dtype == 0 ? 8 : 4;
-    return static_cast<char *>(h->d_Q[dtype]) + es * (size_t)i * (size_t)h->dim;
+    return static_cast<char *>(h->d_Q[dtype]) + es * (size_t)i * (size_t)h->ldq;
 }
 
 struct CycleStats {
@@ -312,12 +317,16 @@ struct CycleStats {
 };
 
 // One Lanczos step i on storage type dtype (Algorithm 2 with full
-// reorthogonalisation, Sec. 3.4): p = H q_i; alpha = q_i^T p; the three-term
-// recurrence p -= alpha q_i + beta_{i-1} q_{i-1} fused with the projections
-// c = Q^T p of one Gram-Schmidt pass against every stored vector; p -= Q c with
-// ||p||^2; then alpha_i = alpha + c_i, beta_i = ||p|| (finalize).  The
-// recurrence followed by the full pass is Gram-Schmidt applied twice.  Every
-// kernel is skipped once S->broken is set (breakdown earlier in the cycle).
+// reorthogonalisation, Sec. 3.4), three launches:
+//   1. p = H q_i and alpha = q_i^T p (the dot fused into the H*x launch);
+//   2. the three-term recurrence p -= alpha q_i + beta_{i-1} q_{i-1} fused with
+//      the projections c = Q^T p of one Gram-Schmidt pass against every stored
+//      vector;
+//   3. p -= Q c with ||p||^2, then alpha_i = alpha + c_i, beta_i = ||p||.
+// The recurrence followed by the full pass is Gram-Schmidt applied twice.  The
+// sums of launches 2 and 3 are finished by their last CTA (no separate
+// reduction launch).  Every kernel is skipped once S->broken is set
+// (breakdown earlier in the cycle).
 int lanczos_step(pairdiag *h, int dtype, int i)
 {
     const int64_t dim = h->dim;
@@ -326,11 +335,11 @@ int lanczos_step(pairdiag *h, int dtype, int i)
     void *Q = h->d_Q[dtype];
     void *p = h->d_p[dtype];
     cudaStream_t st = h->st;
-    PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip));
-    PD_CUDA(multidot_launch(dtype, qvec(h, dtype, i), dim, 1, p, dim, h->d_part, S->c1, st, skip));
-    PD_CUDA(recur_project_launch(dtype, Q, dim, i, S, p, dim, h->d_part, S->c2, st, skip));
-    PD_CUDA(update_launch(dtype, Q, dim, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip));
-    PD_CUDA(finalize_step_launch(S, i, st));
+    const int64_t ld = h->ldq;
+    unsigned long long *tk = &h->d_tk->vec_done;
+    PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip, S->c1));
+    PD_CUDA(recur_project_launch(dtype, Q, ld, i, S, p, dim, h->d_part, S->c2, st, skip, tk));
+    PD_CUDA(update_launch(dtype, Q, ld, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip, tk, S, i));
     return PD_OK;
 }
 
@@ -348,7 +357,8 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     void *p = h->d_p[dtype];
     const int *skip = &S->broken;
     // normalise the start vector
-    PD_CUDA(multidot_launch(dtype, Q, dim, 1, Q, dim, h->d_part, &S->dots[0], st));
+    unsigned long long *tk = &h->d_tk->vec_done;
+    PD_CUDA(multidot_launch(dtype, Q, h->ldq, 1, Q, dim, h->d_part, &S->dots[0], st, nullptr, tk));
     PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
     std::vector<double> history;                  // |beta_1/alpha_1| per cycle
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
@@ -379,7 +389,7 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
             PD_TRY(lanczos_step(h, dtype, i));
         }
         PD_CUDA(tridiag_launch(S, 0, st));
-        PD_CUDA(ritz_launch(dtype, Q, dim, &S->used, S->s, dim, h->d_part, &S->norm2, st));
+        PD_CUDA(ritz_launch(dtype, Q, h->ldq, &S->used, S->s, dim, h->d_part, &S->norm2, st, tk));
         PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->norm2, 1, st));
         double th[2];
         int used = 0;
@@ -453,14 +463,15 @@ int rayleigh64(pairdiag *h, int dtype, double *lambda, double *rel)
     PD_CUDA(convert_launch(0, h->d_v64, dtype, qvec(h, dtype, 0), dim, h->st));
     PD_TRY(hx(h, 0, h->d_v64, h->d_w64));
     LanczosScalars *S = h->d_S;
-    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_w64, dim, h->d_part, &S->dots[0], h->st));
-    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &S->dots[1], h->st));
+    unsigned long long *tk = &h->d_tk->vec_done;
+    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_w64, dim, h->d_part, &S->dots[0], h->st, nullptr, tk));
+    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &S->dots[1], h->st, nullptr, tk));
     double vv_vw[2];
     PD_CUDA(cudaMemcpyAsync(vv_vw, &S->dots[0], 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
     const double lam = vv_vw[0] / vv_vw[1];
     PD_CUDA(cudaMemcpyAsync(&S->dots[2], &lam, sizeof(double), cudaMemcpyHostToDevice, h->st));
-    PD_CUDA(residual_launch(h->d_w64, h->d_v64, &S->dots[2], nullptr, dim, h->d_part, &S->dots[3], h->st));
+    PD_CUDA(residual_launch(h->d_w64, h->d_v64, &S->dots[2], nullptr, dim, h->d_part, &S->dots[3], h->st, tk));
     double r2;
     PD_CUDA(cudaMemcpyAsync(&r2, &S->dots[3], sizeof(double), cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
@@ -531,7 +542,8 @@ int ground_state_impl(pairdiag *h, double tol, double *e0, double *vec_dev, bool
     // output vector
     const double *src = final_dtype == -1 ? h->d_v64 : static_cast<const double *>(qvec(h, 0, 0));
     if (final_dtype == -1) {                   // normalise the refined FP64 copy
-        PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &h->d_S->dots[0], h->st));
+        PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &h->d_S->dots[0], h->st, nullptr,
+                                &h->d_tk->vec_done));
         PD_CUDA(scale_launch(0, h->d_v64, h->d_v64, dim, &h->d_S->dots[0], 1, h->st));
     }
     if (vec_dev) PD_CUDA(cudaMemcpyAsync(vec_dev, src, sizeof(double) * dim, cudaMemcpyDeviceToDevice, h->st));
@@ -635,7 +647,10 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
         if ((st = upload(&h->d_d64, h->d)) != PD_OK) break;
         if ((st = upload(&h->d_G32, G32)) != PD_OK) break;
         if ((st = upload(&h->d_d32, d32)) != PD_OK) break;
-        if ((st = dalloc(&h->d_counter, 4)) != PD_OK) break;
+        if ((st = dalloc(&h->d_tk, 1)) != PD_OK) break;
+        if (cudaMemset(h->d_tk, 0, sizeof(Tickets)) != cudaSuccess) { st = fail(PD_ECUDA, "memset"); break; }
+        if ((st = dalloc(&h->d_blkdot, (size_t)h->B.nblocks)) != PD_OK) break;
+        h->ldq = (h->dim + 3) / 4 * 4;
         h->hxgrid[0] = hx_grid(h->B, 0);
         h->hxgrid[1] = hx_grid(h->B, 1);
         h->rgrid = (int)std::min<int64_t>(h->B.nblocks, 152 * 4);
@@ -822,7 +837,8 @@ int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, i
 {
     if (!h || !Q_dev || !p_dev || !out) return fail(PD_EINVAL, "null argument");
     if (m < 1 || m > kMaxWindow || n < 0 || (dtype != 0 && dtype != 1)) return fail(PD_EINVAL, "bad sizes");
-    PD_CUDA(multidot_launch(dtype, Q_dev, ld, m, p_dev, n, h->d_part, h->d_S->c1, h->st));
+    PD_CUDA(multidot_launch(dtype, Q_dev, ld, m, p_dev, n, h->d_part, h->d_S->c1, h->st, nullptr,
+                            &h->d_tk->vec_done));
     PD_CUDA(cudaMemcpyAsync(out, h->d_S->c1, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
     return PD_OK;

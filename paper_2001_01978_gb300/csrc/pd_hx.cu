@@ -82,6 +82,36 @@ __device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
 // One basis block (high word h, first index base) of y = H x.  x and y point at
 // the problem's own vector; sG/sd/sRank hold its G, d and rank table.  Called
 // by every thread of the CTA (it contains barriers).
+// x^T y over one basis block (this CTA's rows; y as stored), into *out (thread 0)
+template <typename T, typename A, int R>
+__device__ __forceinline__ void block_dot(const A *acc, const T *sx, int nk, double *out, double *sred)
+{
+    DotAcc<T> d;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = threadIdx.x + i * kThreads;
+        if (r < nk) d.add(sx[r], T(acc[i]));
+    }
+    const double s = block_reduce(d, sred);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// End of a persistent H*x launch, called by every CTA: the last one to arrive
+// returns the work counter to zero and adds the per-block dot products in
+// block order (a fixed order, so alpha does not depend on the schedule).
+__device__ __forceinline__ void hx_finish(Tickets *tk, int64_t nblocks, const double *blk_part, double *dot_out,
+                                          double *sred)
+{
+    if (!arrive_last(&tk->hx_done)) return;
+    if (threadIdx.x == 0) tk->hx_next = 0ull;
+    if (!blk_part) return;
+    double s = 0.0;
+#pragma unroll 8
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(blk_part + b);
+    s = block_sum(s, sred);
+    if (threadIdx.x == 0) *dot_out = s;
+}
+
 template <typename T, typename A, int R>
 __device__ __forceinline__ void hx_block(const int omega, const int L, const int H, const int N,
                                          const uint64_t h, const uint64_t base,
@@ -89,7 +119,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
                                          const uint64_t *__restrict__ binom,
                                          const A *sG, const A *sd, const uint16_t *sRank, T *sx, T *sxn,
                                          HHop<A> *sHH, uint64_t *sMX, const T *__restrict__ x,
-                                         T *__restrict__ y)
+                                         T *__restrict__ y, double *blk_dot, double *sred)
 {
     const int tid = threadIdx.x;
     const uint32_t maskL = (1u << L) - 1u;
@@ -223,17 +253,19 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         const int r = tid + i * kThreads;
         if (r < nk) y[base + r] = T(acc[i]);
     }
+    if (blk_dot) block_dot<T, A, R>(acc, sx, nk, blk_dot, sred);
 }
 
 template <typename T, typename A, int R>
 __global__ void __launch_bounds__(kThreads)
 hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
-          const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
-          const int *__restrict__ skip)
+          const T *__restrict__ x, T *__restrict__ y, Tickets *tk, const int *__restrict__ skip,
+          double *blk_part, double *dot_out)
 {
     if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_next;
+    __shared__ double sred[kThreads / 32];
     const int omega = B.omega, L = B.L, H = B.H, N = B.n;
     const Layout lay = layout<T, A>(omega, L, H, B.max_block, B.max_hh);
     A *sG = reinterpret_cast<A *>(smem + lay.G);
@@ -251,14 +283,15 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 
     for (;;) {
         __syncthreads();                          // smem of the previous block is free
-        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        if (tid == 0) s_next = (long long)atomicAdd(&tk->hx_next, 1ull);
         __syncthreads();
         const long long b = s_next;
         if (b >= B.nblocks) break;
 
         hx_block<T, A, R>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
-                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y);
+                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? blk_part + b : nullptr, sred);
     }
+    hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
 
 // ---- batched: blocks of many problems in one launch ----------------------------
@@ -307,7 +340,7 @@ hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__res
         }
         hx_block<T, A, R>(dsc.omega, dsc.L, dsc.omega - dsc.L, dsc.n, __ldg(BB.blk_h + b), __ldg(BB.blk_base + b),
                           BB.lowword_all + dsc.tab_off, BB.binom, sG, sd, sRank, sx, sxn, sHH, sMX,
-                          x + dsc.vec_off, y + dsc.vec_off);
+                          x + dsc.vec_off, y + dsc.vec_off, nullptr, nullptr);
     }
 }
 
@@ -347,12 +380,13 @@ __host__ __device__ inline Layout2 layout2(int omega, int L, int H, int max_bloc
 template <typename T, typename A, int R>
 __global__ void __launch_bounds__(kThreads)
 hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
-           const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
-           const int *__restrict__ skip)
+           const T *__restrict__ x, T *__restrict__ y, Tickets *tk, const int *__restrict__ skip,
+           double *blk_part, double *dot_out)
 {
     if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_next;
+    __shared__ double sred[kThreads / 32];
     const int omega = B.omega, L = B.L, H = B.H, N = B.n, MB = B.max_block;
     const Layout2 lay = layout2<T, A>(omega, L, H, MB, B.max_hh);
     A *sGL = reinterpret_cast<A *>(smem + lay.gl);
@@ -376,7 +410,7 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 
     for (;;) {
         __syncthreads();                          // smem of the previous block is free
-        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        if (tid == 0) s_next = (long long)atomicAdd(&tk->hx_next, 1ull);
         __syncthreads();
         const long long b = s_next;
         if (b >= B.nblocks) break;
@@ -535,7 +569,9 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
             const int r = tid + i * kThreads;
             if (r < nk) y[base + r] = T(acc[i]);
         }
+        if (blk_part) block_dot<T, A, R>(acc, sx, nk, blk_part + b, sred);
     }
+    hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
 
 constexpr size_t kSmemLimit = 200 * 1024;
@@ -565,34 +601,34 @@ size_t kernel_smem(const Blocks &B)
 
 template <typename T, typename A, int R>
 cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, void *y,
-                     unsigned long long *counter, int grid, cudaStream_t st, const int *skip)
+                     Tickets *tk, int grid, cudaStream_t st, const int *skip, const HxDot *dot)
 {
     const size_t smem = kernel_smem<T, A>(B);
     const bool v2 = use_v2<T, A>(B);
     cudaError_t err = cudaFuncSetAttribute(kernel_fn<T, A, R>(B),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-    if (err != cudaSuccess) return err;
+    double *bp = dot ? dot->blk_part : nullptr;
+    double *out = dot ? dot->out : nullptr;
     if (v2)
         hx2_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                          static_cast<T *>(y), counter, skip);
+                                                          static_cast<T *>(y), tk, skip, bp, out);
     else
         hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                         static_cast<T *>(y), counter, skip);
+                                                         static_cast<T *>(y), tk, skip, bp, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T, typename A>
 cudaError_t launch_prec(const Blocks &B, const A *G, const A *d, const void *x, void *y,
-                        unsigned long long *counter, int grid, cudaStream_t st, const int *skip)
+                        Tickets *tk, int grid, cudaStream_t st, const int *skip, const HxDot *dot)
 {
     const int rows = (B.max_block + kThreads - 1) / kThreads;
-    if (rows <= 1) return launch_t<T, A, 1>(B, G, d, x, y, counter, grid, st, skip);
-    if (rows <= 2) return launch_t<T, A, 2>(B, G, d, x, y, counter, grid, st, skip);
-    if (rows <= 4) return launch_t<T, A, 4>(B, G, d, x, y, counter, grid, st, skip);
-    return launch_t<T, A, 8>(B, G, d, x, y, counter, grid, st, skip);
+    if (rows <= 1) return launch_t<T, A, 1>(B, G, d, x, y, tk, grid, st, skip, dot);
+    if (rows <= 2) return launch_t<T, A, 2>(B, G, d, x, y, tk, grid, st, skip, dot);
+    if (rows <= 4) return launch_t<T, A, 4>(B, G, d, x, y, tk, grid, st, skip, dot);
+    return launch_t<T, A, 8>(B, G, d, x, y, tk, grid, st, skip, dot);
 }
 
 template <typename T, typename A>
@@ -732,11 +768,11 @@ int hx_grid(const Blocks &B, int precision)
 }
 
 cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
-                      int *counter, int grid, cudaStream_t st, const int *skip)
+                      Tickets *tk, int grid, cudaStream_t st, const int *skip, const HxDot *dot)
 {
-    auto *ctr = reinterpret_cast<unsigned long long *>(counter);
-    if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, ctr, grid, st, skip);
-    return launch_prec<float, float>(B, P.G32, P.d32, x, y, ctr, grid, st, skip);
+    if (dot && (!dot->blk_part || !dot->out)) return cudaErrorInvalidValue;
+    if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, tk, grid, st, skip, dot);
+    return launch_prec<float, float>(B, P.G32, P.d32, x, y, tk, grid, st, skip, dot);
 }
 
 namespace {

@@ -45,6 +45,7 @@ extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(int n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int kMaxOmega = 62;
+constexpr int kPackBytes = 16;       // streaming kernels move 16-byte packs of vector elements
 constexpr int kMaxLow = 13;          // L <= 13: rank table of 2^L uint16 in shared memory
 constexpr int kMaxWindow = 64;       // Lanczos vectors per cycle
 constexpr int kBinomStride = 64;     // binom[n * 64 + m] = C(n, m)
@@ -84,6 +85,144 @@ struct BatchBlocks {
     int max_omega, max_L, max_H, max_block, max_hh;   // bounds for the shared-memory layout
 };
 
+// Counters of a handle's kernels (device memory, zero when allocated).  Every
+// kernel that uses a field leaves it at zero when it finishes: the CTA that
+// arrives last resets it, so no memset is needed between launches.
+struct Tickets {
+    unsigned long long hx_next;      // next block of a persistent H*x launch
+    unsigned long long hx_done;      // CTAs of that launch that have finished
+    unsigned long long vec_done;     // CTAs of a streaming kernel whose partial sums are written
+    unsigned long long pad;
+};
+
+#ifdef __CUDACC__
+// ---- device reductions shared by the kernels ---------------------------------
+// Float-float accumulation of exact products with FP32 instructions only:
+// a*b = p + pe exactly (FMA), and (hi, lo) += p + pe with Knuth's TwoSum.  This
+// gives close to FP64 accuracy for dot products of FP32 vectors without FP64
+// arithmetic, which GB300 executes at a small fraction of its FP32 rate.
+__device__ __forceinline__ void ff_add_prod(float &hi, float &lo, float a, float b)
+{
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float t = hi + p;
+    const float z = t - hi;
+    const float e = (hi - (t - z)) + (p - z);
+    hi = t;
+    lo += e + pe;
+}
+
+// (ah, al) += (bh, bl) in float-float arithmetic (TwoSum, then renormalised)
+__device__ __forceinline__ void ff_add(float &ah, float &al, float bh, float bl)
+{
+    const float s = ah + bh;
+    const float z = s - ah;
+    float e = (ah - (s - z)) + (bh - z);
+    e += al + bl;
+    const float h = s + e;
+    al = e - (h - s);
+    ah = h;
+}
+
+// block-wide sum of one double per thread; result valid in thread 0.
+// sh: at least blockDim.x / 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+// block-wide float-float sum, converted to double once (thread 0 holds it):
+// the whole reduction tree stays on the FP32 pipes.  sh: blockDim.x / 16 floats.
+__device__ __forceinline__ double block_sum_ff(float hi, float lo, float *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, oh, ol);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) { sh[2 * w] = hi; sh[2 * w + 1] = lo; }
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        float th = 0.0f, tl = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ff_add(th, tl, sh[2 * i], sh[2 * i + 1]);
+        r = (double)th + (double)tl;
+    }
+    return r;
+}
+
+// dot-product accumulator of a storage type: FP64 FMAs for double, float-float
+// (exact products, TwoSum) for float
+template <typename T>
+struct DotAcc {
+    double v = 0.0;
+    __device__ __forceinline__ void add(T a, T b) { v = fma((double)a, (double)b, v); }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct DotAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(hi, lo, a, b); }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+// block-wide sum of the accumulators (thread 0); sh: blockDim.x / 32 doubles
+__device__ __forceinline__ double block_reduce(const DotAcc<double> &a, double *sh) { return block_sum(a.get(), sh); }
+__device__ __forceinline__ double block_reduce(const DotAcc<float> &a, double *sh)
+{
+    return block_sum_ff(a.hi, a.lo, reinterpret_cast<float *>(sh));
+}
+
+// Called by every thread of every CTA after thread 0 has written the CTA's
+// partial sums.  Returns true in the one CTA that arrives last; by then the
+// partial sums of all CTAs are visible to it (read them with __ldcg).  That CTA
+// returns the ticket to zero.  No CTA waits for another.
+__device__ __forceinline__ bool arrive_last(unsigned long long *ticket)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();                                       // release this CTA's partial sums
+        const unsigned long long t = atomicAdd(ticket, 1ull);
+        const int last = (t == (unsigned long long)gridDim.x - 1ull);
+        if (last) {
+            *ticket = 0ull;
+            __threadfence();                                   // acquire the others'
+        }
+        s_last = last;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// out[j] = sum_b part[b * kMaxWindow + j] for j < m: warp w takes outputs w,
+// w + warps, ...; each lane a fixed strided subset of b, then a fixed xor tree,
+// so the order of the additions never changes.  Returns out[0] in thread 0.
+__device__ __forceinline__ double reduce_partials(const double *part, int nb, int m, double *out)
+{
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    double first = 0.0;
+    for (int j = (int)(threadIdx.x >> 5); j < m; j += nw) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < nb; b += 32) s += __ldcg(part + (int64_t)b * kMaxWindow + j);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[j] = s;
+        if (j == 0) first = s;
+    }
+    return first;
+}
+#endif  // __CUDACC__
+
 // ---- H*x (pd_hx.cu) -------------------------------------------------------
 // precision 0: double vectors / double accumulation with G64, d64
 // precision 1: float vectors / float accumulation with G32, d32
@@ -97,9 +236,18 @@ cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int preci
 int hx_batch_grid(const BatchBlocks &BB, int precision);
 size_t hx_smem_bytes(const Blocks &B, int precision);
 int hx_variant(const Blocks &B, int precision);   // kernel variant a launch will use (1 or 2)
-// skip (nullable, device): when *skip != 0 the launched kernels return at once
+// y = H x (Eq. 2 in the pair basis) over the persistent grid.
+// skip (nullable, device): when *skip != 0 the launched kernels return at once.
+// dot (nullable): also x^T y, the Lanczos alpha, with one partial sum per basis
+// block in dot->blk_part[B.nblocks]; the last CTA adds them in block order into
+// *dot->out (deterministic).
+struct HxDot {
+    double *blk_part;
+    double *out;
+};
 cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const void *x, void *y,
-                      int *counter, int grid, cudaStream_t st, const int *skip = nullptr);
+                      Tickets *tk, int grid, cudaStream_t st, const int *skip = nullptr,
+                      const HxDot *dot = nullptr);
 int hx_grid(const Blocks &B, int precision);
 // Monopole_Min/Max/Posit_Min: partials[grid*3] scratch; out[0]=min, out[1]=max, out[2]=pos (as double bits)
 cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,
@@ -129,13 +277,23 @@ struct LanczosScalars {              // lives in device memory
     int    broken;                   // breakdown seen: later steps of the cycle are skipped
 };
 int vec_grid();                      // CTAs of the streaming vector kernels
-// partial results of the streaming kernels: [vec_grid() * kMaxWindow] doubles
+// Streaming kernels: vectors of n elements; Q holds vectors j at Q + j*ld.  They
+// move 16-byte packs when every vector is 16-byte aligned (ld a multiple of the
+// pack), else single elements.  partials: [vec_grid() * kMaxWindow] doubles.
+// ticket (nullable): with a ticket the last CTA adds the partial sums itself;
+// without one a separate one-CTA reduction is launched.
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
-                            double *partials, double *out, cudaStream_t st, const int *skip = nullptr);
-// p -= sum_j c[j] Q_j; if norm_out != nullptr also ||p||^2 -> *norm_out
+                            double *partials, double *out, cudaStream_t st, const int *skip = nullptr,
+                            unsigned long long *ticket = nullptr);
+// p -= sum_j c[j] Q_j; if norm_out != nullptr also ||p||^2 -> *norm_out.
+// fin (nullable, needs norm_out and ticket): the Lanczos step bookkeeping of
+// step fin_i, done by the last CTA: alpha[i] = c1[0] + c2[i], beta[i] =
+// sqrt(norm2), used = i + 1; broken is set when beta[i] <= 1e-13 * tnorm (an
+// invariant subspace was found).
 cudaError_t update_launch(int dtype, const void *Q, int64_t ld, int m, const double *c, void *p,
                           int64_t n, double *partials, double *norm_out, cudaStream_t st,
-                          const int *skip = nullptr);
+                          const int *skip = nullptr, unsigned long long *ticket = nullptr,
+                          struct LanczosScalars *fin = nullptr, int fin_i = 0);
 // dst = src * (1 / sqrt(*norm2)) (or src / *beta when is_norm == 0)
 cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const double *div,
                          int div_is_norm2, cudaStream_t st, const int *skip = nullptr);
@@ -143,10 +301,7 @@ cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const
 // out[j] = Q_j^T p for j <= i (the projections of one full Gram-Schmidt pass)
 cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, const LanczosScalars *S,
                                  void *p, int64_t n, double *partials, double *out, cudaStream_t st,
-                                 const int *skip = nullptr);
-// Lanczos step bookkeeping: alpha[i] = c1[0]+c2[i], beta[i] = sqrt(norm2), used = i+1;
-// sets broken when beta[i] <= 1e-13 * tnorm (an invariant subspace was found)
-cudaError_t finalize_step_launch(LanczosScalars *S, int i, cudaStream_t st);
+                                 const int *skip = nullptr, unsigned long long *ticket = nullptr);
 // start of a cycle: used = 0, broken = 0, tnorm = 0
 cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
 // lowest two eigenvalues + lowest eigenvector of tridiag(alpha, beta) -> S->theta, S->s;
@@ -154,13 +309,15 @@ cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
 cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st);
 // Q0 = sum_j s_j Q_j (in place) for j < *m_dev, ||Q0||^2 -> *norm_out
 cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, const int *m_dev, const double *s, int64_t n,
-                        double *partials, double *norm_out, cudaStream_t st);
+                        double *partials, double *norm_out, cudaStream_t st,
+                        unsigned long long *ticket = nullptr);
 cudaError_t random_start_launch(int dtype, void *q, int64_t n, uint64_t seed, cudaStream_t st);
 cudaError_t convert_launch(int dst_dtype, void *dst, int src_dtype, const void *src, int64_t n,
                            cudaStream_t st);
 // dst = a - lambda * b (double), ||dst||^2 -> *norm_out; lambda read from device
 cudaError_t residual_launch(const double *a, const double *b, const double *lambda, double *dst,
-                            int64_t n, double *partials, double *norm_out, cudaStream_t st);
+                            int64_t n, double *partials, double *norm_out, cudaStream_t st,
+                            unsigned long long *ticket = nullptr);
 
 // ---- batched Lanczos (pd_lanczos.cu kernels, pd_batch.cu driver) -------------
 struct BatchState {                  // one problem (device memory)

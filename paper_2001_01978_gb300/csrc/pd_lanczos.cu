@@ -10,302 +10,277 @@
 
 #include <cfloat>
 #include <cmath>
+#include <cstdint>
+#include <initializer_list>
 
 namespace pd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kGroup = 8;             // vectors handled per pass of a multi-dot
+constexpr int kGroup = 8;             // vectors handled per pass of a multi-vector kernel
 constexpr int kGrid = 152 * 4;
 
-__device__ __forceinline__ double ld(const double *p, int64_t i) { return __ldg(p + i); }
-
-// block-wide sum of one double per thread; result valid in thread 0
-__device__ __forceinline__ double block_sum(double v, double *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
-    return s;
-}
-
-// partial[b*kMaxWindow + j] = sum over this CTA's elements of Q_j[i] p[i]
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-multidot_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p, int64_t n,
-                double *__restrict__ part, const int *__restrict__ skip)
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+
+// ---- packs: W consecutive elements moved as one 16-byte access --------------
+// W = 16 / sizeof(T) when every vector of a launch is 16-byte aligned, else 1.
+// Pack c holds elements c*W .. c*W+W-1; the last pack of a vector whose length
+// is not a multiple of W is read element by element (zero past the end) and
+// written element by element, so n need not be a multiple of W.
+template <typename T, int W>
+struct Pack {
+    T v[W];
+};
+
+template <typename T> struct Wide;
+template <> struct Wide<float> { using type = float4; };
+template <> struct Wide<double> { using type = double2; };
+
+template <typename T, int W, bool RO>
+__device__ __forceinline__ Pack<T, W> load_pack(const T *a, int64_t c, int64_t n)
 {
-    if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int j0 = 0; j0 < m; j0 += kGroup) {
-        double acc[kGroup];
+    Pack<T, W> r;
+    const int64_t e = c * W;
+    if constexpr (W > 1) {
+        static_assert(sizeof(T) * W == kPackBytes, "pack width");
+        if (e + W <= n) {
+            using V = typename Wide<T>::type;
+            const V *pv = reinterpret_cast<const V *>(a) + c;
+            const V t = RO ? __ldg(pv) : *pv;
+            const T *tv = reinterpret_cast<const T *>(&t);
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) acc[u] = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-            const double pv = ld(p, i);
-#pragma unroll
-            for (int u = 0; u < kGroup; ++u)
-                if (j0 + u < m) acc[u] += ld(Q, (int64_t)(j0 + u) * ldq + i) * pv;
+            for (int k = 0; k < W; ++k) r.v[k] = tv[k];
+            return r;
         }
+    }
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            if (j0 + u < m) {
-                const double s = block_sum(acc[u], sh);
-                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
-            }
-        }
-    }
-}
-
-// Float-float accumulation of exact products with FP32 instructions only:
-// a*b = p + pe exactly (FMA), and (hi, lo) += p + pe with Knuth's TwoSum.  This
-// gives close to FP64 accuracy for dot products of FP32 vectors without FP64
-// arithmetic, which GB300 executes at a small fraction of its FP32 rate.
-__device__ __forceinline__ void ff_add_prod(float &hi, float &lo, float a, float b)
-{
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);
-    const float t = hi + p;
-    const float z = t - hi;
-    const float e = (hi - (t - z)) + (p - z);
-    hi = t;
-    lo += e + pe;
-}
-
-// (ah, al) += (bh, bl) in float-float arithmetic (TwoSum, then renormalised)
-__device__ __forceinline__ void ff_add(float &ah, float &al, float bh, float bl)
-{
-    const float s = ah + bh;
-    const float z = s - ah;
-    float e = (ah - (s - z)) + (bh - z);
-    e += al + bl;
-    const float h = s + e;
-    al = e - (h - s);
-    ah = h;
-}
-
-// block-wide float-float sum, converted to double once (thread 0 holds it):
-// the whole reduction tree stays on the FP32 pipes
-__device__ __forceinline__ double block_sum_ff(float hi, float lo, float *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
-        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
-        ff_add(hi, lo, oh, ol);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) { sh[2 * w] = hi; sh[2 * w + 1] = lo; }
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        float th = 0.0f, tl = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ff_add(th, tl, sh[2 * i], sh[2 * i + 1]);
-        r = (double)th + (double)tl;
-    }
+    for (int k = 0; k < W; ++k) r.v[k] = (e + k < n) ? (RO ? __ldg(a + e + k) : a[e + k]) : T(0);
     return r;
 }
 
-// multi-dot of FP32 vectors, float-float per thread, FP64 across threads
-__global__ void __launch_bounds__(kThreads)
-multidot_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const float *__restrict__ p, int64_t n,
-                    double *__restrict__ part, const int *__restrict__ skip)
+template <typename T, int W>
+__device__ __forceinline__ void store_pack(T *a, int64_t c, int64_t n, const Pack<T, W> &r)
 {
-    if (skip && *skip) return;
-    __shared__ float sh[2 * (kThreads / 32)];
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int j0 = 0; j0 < m; j0 += kGroup) {
-        float hi[kGroup], lo[kGroup];
+    const int64_t e = c * W;
+    if constexpr (W > 1) {
+        if (e + W <= n) {
+            using V = typename Wide<T>::type;
+            V t;
+            T *tv = reinterpret_cast<T *>(&t);
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) hi[u] = lo[u] = 0.0f;
-        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-            const float pv = __ldg(p + i);
-#pragma unroll
-            for (int u = 0; u < kGroup; ++u)
-                if (j0 + u < m) ff_add_prod(hi[u], lo[u], __ldg(Q + (int64_t)(j0 + u) * ldq + i), pv);
-        }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            if (j0 + u < m) {
-                const double s = block_sum_ff(hi[u], lo[u], sh);
-                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
-            }
+            for (int k = 0; k < W; ++k) tv[k] = r.v[k];
+            reinterpret_cast<V *>(a)[c] = t;
+            return;
         }
     }
-}
-
-// Lanczos recurrence fused with the projections of one Gram-Schmidt pass:
-//   p <- p - alpha q_i - beta_{i-1} q_{i-1}   (Algorithm 2; alpha = S->c1[0])
-//   part <- per-CTA partial sums of Q_j^T p for j <= i (after the update)
-// Elements are visited in the same order by the same thread in every group, so
-// the groups after the first read back this thread's own updated values.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosScalars *__restrict__ S,
-                     T *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];          // also holds the float pairs of block_sum_ff
-    const int m = i + 1;
-    const T a = (T)S->c1[0];
-    const T b = (T)(i > 0 ? S->beta[i - 1] : 0.0);
-    const T *qi = Q + (int64_t)i * ldq;
-    const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int j0 = 0; j0 < m; j0 += kGroup) {
-        float hi[kGroup], lo[kGroup];     // used by the FP32 path
-        double acc[kGroup];               // used by the FP64 path
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) { hi[u] = lo[u] = 0.0f; acc[u] = 0.0; }
-        for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n; e += stride) {
-            T v;
-            if (j0 == 0) {
-                v = p[e];
-                if constexpr (sizeof(T) == 4) {
-                    v = fmaf(-a, __ldg(qi + e), v);
-                    if (i > 0) v = fmaf(-b, __ldg(qm + e), v);
-                } else {
-                    v = fma(-a, __ldg(qi + e), v);
-                    if (i > 0) v = fma(-b, __ldg(qm + e), v);
-                }
-                p[e] = v;
-            } else {
-                v = p[e];
-            }
-#pragma unroll
-            for (int u = 0; u < kGroup; ++u) {
-                if (j0 + u < m) {
-                    const T q = __ldg(Q + (int64_t)(j0 + u) * ldq + e);
-                    if constexpr (sizeof(T) == 4) ff_add_prod(hi[u], lo[u], q, v);
-                    else acc[u] = fma((double)q, (double)v, acc[u]);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            if (j0 + u < m) {
-                double s;
-                if constexpr (sizeof(T) == 4) s = block_sum_ff(hi[u], lo[u], reinterpret_cast<float *>(sh));
-                else s = block_sum(acc[u], sh);
-                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
-            }
-        }
-    }
+    for (int k = 0; k < W; ++k)
+        if (e + k < n) a[e + k] = r.v[k];
 }
 
-// out[j] = sum_b part[b*kMaxWindow + j]: one warp per output, each lane a fixed
-// strided subset, then a fixed xor-shuffle tree (deterministic)
-__global__ void reduce_kernel(const double *__restrict__ part, int nb, int m, double *__restrict__ out,
-                              const int *__restrict__ skip)
+// Lanczos step bookkeeping (Algorithm 2): alpha_i = alpha + c_i (the second
+// Gram-Schmidt pass corrects the recurrence's alpha), beta_i = ||p||; a beta_i
+// below 1e-13 of the running matrix-norm estimate ends the cycle (an invariant
+// subspace, or a NaN).
+__device__ __forceinline__ void finalize_step(LanczosScalars *S, int i, double norm2)
 {
-    if (skip && *skip) return;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (j >= m) return;
-    double s = 0.0;
-#pragma unroll 4
-    for (int b = lane; b < nb; b += 32) s += part[b * kMaxWindow + j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[j] = s;
-}
-
-inline void reduce(const double *part, int nb, int m, double *out, cudaStream_t st, const int *skip = nullptr)
-{
-    reduce_kernel<<<(m + 7) / 8, 256, 0, st>>>(part, nb, m, out, skip);
-}
-
-// p -= sum_j c_j Q_j ; optional ||p||^2 partials (of the stored, rounded values)
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-update_kernel(const T *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ c,
-              T *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    __shared__ double sc[kMaxWindow];
-    __shared__ double sh[kThreads / 32];
-    for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = c[j];
-    __syncthreads();
-    double nrm = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-        double v = (double)p[i];
-        for (int j = 0; j < m; ++j) v -= sc[j] * ld(Q, (int64_t)j * ldq + i);
-        const T t = (T)v;
-        p[i] = t;
-        nrm += (double)t * (double)t;
-    }
-    if (part) {
-        const double s = block_sum(nrm, sh);
-        if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
-    }
-}
-
-// p -= sum_j c_j Q_j with FP32 FMAs (the result is stored in FP32 anyway; the
-// second Gram-Schmidt pass removes what this rounding leaves along Q)
-__global__ void __launch_bounds__(kThreads)
-update_f32_kernel(const float *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ c,
-                  float *__restrict__ p, int64_t n, double *__restrict__ part, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    __shared__ float sc[kMaxWindow];
-    __shared__ double sh[kThreads / 32];
-    for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = (float)c[j];
-    __syncthreads();
-    float hi = 0.0f, lo = 0.0f;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-        float v = p[i];
-        for (int j = 0; j < m; ++j) v = fmaf(-sc[j], __ldg(Q + (int64_t)j * ldq + i), v);
-        p[i] = v;
-        ff_add_prod(hi, lo, v, v);
-    }
-    if (part) {
-        const double s = block_sum_ff(hi, lo, reinterpret_cast<float *>(sh));
-        if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
-    }
-}
-
-__global__ void scale_f32_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t n,
-                                 const double *__restrict__ div, int is_norm2, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    const double d = is_norm2 ? sqrt(*div) : *div;
-    const float f = (d > 0.0) ? (float)(1.0 / d) : 0.0f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-        dst[i] = src[i] * f;
-}
-
-template <typename T>
-__global__ void scale_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t n,
-                             const double *__restrict__ div, int is_norm2, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    const double d = is_norm2 ? sqrt(*div) : *div;
-    const double f = (d > 0.0) ? 1.0 / d : 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-        dst[i] = (T)((double)src[i] * f);
-}
-
-__global__ void finalize_kernel(LanczosScalars *S, int i)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0 || S->broken) return;
+    if (S->broken) return;
     const double a = S->c1[0] + S->c2[i];
-    const double b = sqrt(S->norm2);
+    const double b = sqrt(norm2);
     S->alpha[i] = a;
     S->beta[i] = b;
     const double row = fabs(a) + b + (i > 0 ? S->beta[i - 1] : 0.0);
     const double tn = fmax(S->tnorm, row);
     S->tnorm = tn;
     S->used = i + 1;
-    if (!(b > 1e-13 * tn)) S->broken = 1;        // invariant subspace found (or a NaN)
+    if (!(b > 1e-13 * tn)) S->broken = 1;
+}
+
+// out[j] = Q_j^T p for j < m (partials per CTA; with a ticket the last CTA adds them)
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads)
+dots_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p, int64_t n,
+            double *__restrict__ part, double *__restrict__ out, unsigned long long *ticket,
+            const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    __shared__ double sh[kThreads / 32];
+    const int64_t nc = (n + W - 1) / W;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t c0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (int j0 = 0; j0 < m; j0 += kGroup) {
+        DotAcc<T> acc[kGroup];
+        for (int64_t c = c0; c < nc; c += stride) {
+            const Pack<T, W> pv = load_pack<T, W, true>(p, c, n);
+            Pack<T, W> q[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m)
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], pv.v[k]);
+        }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+            if (j0 + u < m) {
+                const double s = block_reduce(acc[u], sh);
+                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
+            }
+        }
+    }
+    if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, m, out);
+}
+
+// Lanczos recurrence fused with the projections of one Gram-Schmidt pass:
+//   p <- p - alpha q_i - beta_{i-1} q_{i-1}   (Algorithm 2; alpha = S->c1[0])
+//   out[j] = Q_j^T p for j <= i (after the update)
+// Every pack is visited by the same thread in every group, so the groups after
+// the first read back this thread's own updated values.
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads, 3)
+recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosScalars *__restrict__ S,
+                     T *__restrict__ p, int64_t n, double *__restrict__ part, double *__restrict__ out,
+                     unsigned long long *ticket, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    __shared__ double sh[kThreads / 32];
+    const int m = i + 1;
+    const T a = (T)S->c1[0];
+    const T b = (T)(i > 0 ? S->beta[i - 1] : 0.0);
+    const T *qi = Q + (int64_t)i * ldq;
+    const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
+    T cr[kGroup];                                 // recurrence coefficients of group 0
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) cr[u] = (u == i) ? a : (u == i - 1) ? b : T(0);
+    const int64_t nc = (n + W - 1) / W;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t c0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (int j0 = 0; j0 < m; j0 += kGroup) {
+        DotAcc<T> acc[kGroup];
+        for (int64_t c = c0; c < nc; c += stride) {
+            Pack<T, W> v = load_pack<T, W, false>(p, c, n);
+            Pack<T, W> q[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
+            if (j0 == 0) {
+                if (i < kGroup) {
+                    // q_i and q_{i-1} are packs of this group: one sweep over the
+                    // group, highest index first, whose coefficients vanish except
+                    // at i (alpha) and i-1 (beta), so q_i is applied before q_{i-1}
+#pragma unroll
+                    for (int u = kGroup - 1; u >= 0; --u)
+                        if (u <= i)
+#pragma unroll
+                            for (int k = 0; k < W; ++k) v.v[k] = fma_t<T>(-cr[u], q[u].v[k], v.v[k]);
+                } else {
+                    const Pack<T, W> x = load_pack<T, W, true>(qi, c, n);
+                    const Pack<T, W> y = load_pack<T, W, true>(qm, c, n);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) v.v[k] = fma_t<T>(-b, y.v[k], fma_t<T>(-a, x.v[k], v.v[k]));
+                }
+                store_pack<T, W>(p, c, n, v);
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m)
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], v.v[k]);
+        }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+            if (j0 + u < m) {
+                const double s = block_reduce(acc[u], sh);
+                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
+            }
+        }
+    }
+    if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, m, out);
+}
+
+// out[j] = sum_b part[b*kMaxWindow + j] in one CTA (launches without a ticket)
+__global__ void reduce_kernel(const double *__restrict__ part, int nb, int m, double *__restrict__ out,
+                              const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    reduce_partials(part, nb, m, out);
+}
+
+inline void reduce(const double *part, int nb, int m, double *out, cudaStream_t st, const int *skip = nullptr)
+{
+    reduce_kernel<<<1, 256, 0, st>>>(part, nb, m, out, skip);
+    count_launches(1);
+}
+
+// p -= sum_j c_j Q_j in the storage type (FP32 FMAs for float: the result is
+// stored in FP32 anyway, and the second Gram-Schmidt pass removes what this
+// rounding leaves along Q); optional ||p||^2 of the stored values; optional
+// step bookkeeping by the last CTA
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads)
+update_kernel(const T *__restrict__ Q, int64_t ldq, int m, const double *__restrict__ c,
+              T *__restrict__ p, int64_t n, double *__restrict__ part, double *__restrict__ norm_out,
+              unsigned long long *ticket, const int *__restrict__ skip, LanczosScalars *fin, int fin_i)
+{
+    if (skip && *skip) return;
+    __shared__ T sc[kMaxWindow];
+    __shared__ double sh[kThreads / 32];
+    for (int j = threadIdx.x; j < m; j += kThreads) sc[j] = (T)c[j];
+    __syncthreads();
+    DotAcc<T> nrm;
+    const int64_t nc = (n + W - 1) / W;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < nc; e += stride) {
+        Pack<T, W> v = load_pack<T, W, false>(p, e, n);
+        for (int j0 = 0; j0 < m; j0 += kGroup) {
+            Pack<T, W> q[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, e, n);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m)
+#pragma unroll
+                    for (int k = 0; k < W; ++k) v.v[k] = fma_t<T>(-sc[j0 + u], q[u].v[k], v.v[k]);
+        }
+        store_pack<T, W>(p, e, n, v);
+#pragma unroll
+        for (int k = 0; k < W; ++k) nrm.add(v.v[k], v.v[k]);
+    }
+    if (norm_out) {
+        const double s = block_reduce(nrm, sh);
+        if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
+        if (ticket && arrive_last(ticket)) {
+            const double nn = reduce_partials(part, gridDim.x, 1, norm_out);
+            if (fin && threadIdx.x == 0) finalize_step(fin, fin_i, nn);
+        }
+    }
+}
+
+// dst = src * f with f = 1 / *div (or 1 / sqrt(*div)); src may be dst
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads)
+scale_kernel(const T *src, T *dst, int64_t n, const double *__restrict__ div, int is_norm2,
+             const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const double d = is_norm2 ? sqrt(*div) : *div;
+    const T f = (d > 0.0) ? (T)(1.0 / d) : T(0);
+    const int64_t nc = (n + W - 1) / W;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < nc; c += stride) {
+        Pack<T, W> v = load_pack<T, W, false>(src, c, n);
+#pragma unroll
+        for (int k = 0; k < W; ++k) v.v[k] = v.v[k] * f;
+        store_pack<T, W>(dst, c, n, v);
+    }
 }
 
 __global__ void cycle_reset_kernel(LanczosScalars *S)
@@ -469,49 +444,43 @@ __global__ void tridiag_kernel(LanczosScalars *S, int m)
     tridiag_warp(S->alpha, S->beta, m, S->theta, S->s, a, b, b2, z, u0, u1, u2);
 }
 
-// Q0 <- sum_j s_j Q_j (in place; each element is read before it is written)
-template <typename T>
+// Q0 <- sum_j s_j Q_j for j < *m_dev (in place; each element is read by its own
+// thread before that thread writes it), ||Q0||^2 partials
+template <typename T, int W>
 __global__ void __launch_bounds__(kThreads)
-ritz_kernel(T *__restrict__ Q, int64_t ldq, const int *__restrict__ m_dev, const double *__restrict__ s,
-            int64_t n, double *__restrict__ part)
+ritz_kernel(T *Q, int64_t ldq, const int *__restrict__ m_dev, const double *__restrict__ s, int64_t n,
+            double *__restrict__ part, double *__restrict__ norm_out, unsigned long long *ticket)
 {
     const int m = *m_dev;
-    __shared__ double ss[kMaxWindow];
+    __shared__ T ss[kMaxWindow];
     __shared__ double sh[kThreads / 32];
-    for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = s[j];
+    for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = (T)s[j];
     __syncthreads();
-    double nrm = 0.0;
+    DotAcc<T> nrm;
+    const int64_t nc = (n + W - 1) / W;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-        double v = 0.0;
-        for (int j = 0; j < m; ++j) v += ss[j] * (double)Q[(int64_t)j * ldq + i];
-        const T t = (T)v;
-        Q[i] = t;
-        nrm += (double)t * (double)t;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < nc; e += stride) {
+        Pack<T, W> v;
+#pragma unroll
+        for (int k = 0; k < W; ++k) v.v[k] = T(0);
+        for (int j0 = 0; j0 < m; j0 += kGroup) {
+            Pack<T, W> q[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m) q[u] = load_pack<T, W, false>(Q + (int64_t)(j0 + u) * ldq, e, n);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                if (j0 + u < m)
+#pragma unroll
+                    for (int k = 0; k < W; ++k) v.v[k] = fma_t<T>(ss[j0 + u], q[u].v[k], v.v[k]);
+        }
+        store_pack<T, W>(Q, e, n, v);
+#pragma unroll
+        for (int k = 0; k < W; ++k) nrm.add(v.v[k], v.v[k]);
     }
-    const double sum = block_sum(nrm, sh);
+    const double sum = block_reduce(nrm, sh);
     if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = sum;
-}
-
-__global__ void __launch_bounds__(kThreads)
-ritz_f32_kernel(float *__restrict__ Q, int64_t ldq, const int *__restrict__ m_dev, const double *__restrict__ s,
-                int64_t n, double *__restrict__ part)
-{
-    const int m = *m_dev;
-    __shared__ float ss[kMaxWindow];
-    __shared__ double sh[kThreads / 32];
-    for (int j = threadIdx.x; j < m; j += kThreads) ss[j] = (float)s[j];
-    __syncthreads();
-    float hi = 0.0f, lo = 0.0f;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-        float v = 0.0f;
-        for (int j = 0; j < m; ++j) v = fmaf(ss[j], Q[(int64_t)j * ldq + i], v);
-        Q[i] = v;
-        ff_add_prod(hi, lo, v, v);
-    }
-    const double sum = block_sum_ff(hi, lo, reinterpret_cast<float *>(sh));
-    if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = sum;
+    if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, 1, norm_out);
 }
 
 // counter-based SplitMix64 (Steele, Lea & Flood 2014) -> uniform [-1, 1)
@@ -540,51 +509,35 @@ __global__ void convert_kernel(D *__restrict__ dst, const S *__restrict__ src, i
         dst[i] = (D)src[i];
 }
 
+// r = a - lambda b (FP64), ||r||^2 partials; r stored when dst != nullptr
+template <int W>
 __global__ void __launch_bounds__(kThreads)
 residual_kernel(const double *__restrict__ a, const double *__restrict__ b,
                 const double *__restrict__ lambda, double *__restrict__ dst, int64_t n,
-                double *__restrict__ part)
+                double *__restrict__ part, double *__restrict__ norm_out, unsigned long long *ticket)
 {
     __shared__ double sh[kThreads / 32];
     const double lam = *lambda;
-    double nrm = 0.0;
+    DotAcc<double> nrm;
+    const int64_t nc = (n + W - 1) / W;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) {
-        const double r = a[i] - lam * b[i];
-        if (dst) dst[i] = r;
-        nrm += r * r;
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < nc; c += stride) {
+        const Pack<double, W> x = load_pack<double, W, true>(a, c, n);
+        const Pack<double, W> y = load_pack<double, W, true>(b, c, n);
+        Pack<double, W> r;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            r.v[k] = x.v[k] - lam * y.v[k];
+            nrm.add(r.v[k], r.v[k]);
+        }
+        if (dst) store_pack<double, W>(dst, c, n, r);
     }
-    const double s = block_sum(nrm, sh);
+    const double s = block_reduce(nrm, sh);
     if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow] = s;
+    if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, 1, norm_out);
 }
 
 // ---- batched (segmented) kernels: vectors concatenated over problems ---------
-template <typename T>
-struct DotAcc {                       // FP64 products and sums
-    double v = 0.0;
-    __device__ __forceinline__ void add(T a, T b) { v = fma((double)a, (double)b, v); }
-    __device__ __forceinline__ double get() const { return v; }
-};
-template <>
-struct DotAcc<float> {                // float-float (exact products, TwoSum)
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(hi, lo, a, b); }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
-};
-
-__device__ __forceinline__ double block_reduce(const DotAcc<double> &a, double *sh) { return block_sum(a.get(), sh); }
-__device__ __forceinline__ double block_reduce(const DotAcc<float> &a, double *sh)
-{
-    return block_sum_ff(a.hi, a.lo, reinterpret_cast<float *>(sh));
-}
-
-template <typename T>
-__device__ __forceinline__ T fma_t(T a, T b, T c);
-template <>
-__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <>
-__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ v,
@@ -893,67 +846,150 @@ int grid_for(int64_t n)
     return (int)(g > 0 ? g : 1);
 }
 
+// 16-byte packs when every vector of the launch starts on a 16-byte boundary
+// (and the leading dimension keeps it there); single elements otherwise
+template <typename T>
+bool packable(std::initializer_list<const void *> ptrs, int64_t ld)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    if (ld % W) return false;
+    for (const void *p : ptrs)
+        if (reinterpret_cast<uintptr_t>(p) % kPackBytes) return false;
+    return true;
+}
+
+// CTAs of one wave of a streaming kernel: SMs x resident CTAs per SM (looked up
+// once per kernel), at most kGrid, and no more than the work needs
+template <auto kernel>
+int wave_grid(int64_t units)
+{
+    static const int wave = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        const int w = sms * (per_sm > 0 ? per_sm : 1);
+        return w < kGrid ? w : kGrid;
+    }();
+    const int g = grid_for(units);
+    return g < wave ? g : wave;
+}
+
+template <typename T>
+int64_t pack_units(int64_t n, bool packed)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    return packed ? (n + W - 1) / W : n;
+}
+
+template <typename T>
+void dots_t(const T *Q, int64_t ld, int m, const T *p, int64_t n, double *part, double *out,
+            unsigned long long *ticket, const int *skip, cudaStream_t st)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    const bool pk = packable<T>({Q, p}, ld);
+    const int g = pk ? wave_grid<dots_kernel<T, W>>(pack_units<T>(n, pk)) : wave_grid<dots_kernel<T, 1>>(n);
+    if (pk) dots_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    else dots_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    count_launches(1);
+    if (!ticket) reduce(part, g, m, out, st, skip);
+}
+
+template <typename T>
+void recur_t(const T *Q, int64_t ld, int i, const LanczosScalars *S, T *p, int64_t n, double *part,
+             double *out, unsigned long long *ticket, const int *skip, cudaStream_t st)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    const bool pk = packable<T>({Q, p}, ld);
+    const int g = pk ? wave_grid<recur_project_kernel<T, W>>(pack_units<T>(n, pk))
+                     : wave_grid<recur_project_kernel<T, 1>>(n);
+    if (pk) recur_project_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, i, S, p, n, part, out, ticket, skip);
+    else recur_project_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, i, S, p, n, part, out, ticket, skip);
+    count_launches(1);
+    if (!ticket) reduce(part, g, i + 1, out, st, skip);
+}
+
+template <typename T>
+void update_t(const T *Q, int64_t ld, int m, const double *c, T *p, int64_t n, double *part, double *norm_out,
+              unsigned long long *ticket, const int *skip, LanczosScalars *fin, int fin_i, cudaStream_t st)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    const bool pk = packable<T>({Q, p}, ld);
+    const int g = pk ? wave_grid<update_kernel<T, W>>(pack_units<T>(n, pk)) : wave_grid<update_kernel<T, 1>>(n);
+    if (pk)
+        update_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, m, c, p, n, part, norm_out, ticket, skip, fin, fin_i);
+    else
+        update_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, m, c, p, n, part, norm_out, ticket, skip, fin, fin_i);
+    count_launches(1);
+    if (norm_out && !ticket) reduce(part, g, 1, norm_out, st, skip);
+}
+
+template <typename T>
+void scale_t(const T *src, T *dst, int64_t n, const double *div, int is_norm2, const int *skip, cudaStream_t st)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    const bool pk = packable<T>({src, dst}, 0);
+    const int g = pk ? wave_grid<scale_kernel<T, W>>(pack_units<T>(n, pk)) : wave_grid<scale_kernel<T, 1>>(n);
+    if (pk) scale_kernel<T, W><<<g, kThreads, 0, st>>>(src, dst, n, div, is_norm2, skip);
+    else scale_kernel<T, 1><<<g, kThreads, 0, st>>>(src, dst, n, div, is_norm2, skip);
+    count_launches(1);
+}
+
+template <typename T>
+void ritz_t(T *Q, int64_t ld, const int *m_dev, const double *s, int64_t n, double *part, double *norm_out,
+            unsigned long long *ticket, cudaStream_t st)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    const bool pk = packable<T>({Q}, ld);
+    const int g = pk ? wave_grid<ritz_kernel<T, W>>(pack_units<T>(n, pk)) : wave_grid<ritz_kernel<T, 1>>(n);
+    if (pk) ritz_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, m_dev, s, n, part, norm_out, ticket);
+    else ritz_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, m_dev, s, n, part, norm_out, ticket);
+    count_launches(1);
+    if (!ticket) reduce(part, g, 1, norm_out, st);
+}
+
 }  // namespace
 
 int vec_grid() { return kGrid; }
 
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
-                            double *partials, double *out, cudaStream_t st, const int *skip)
+                            double *partials, double *out, cudaStream_t st, const int *skip,
+                            unsigned long long *ticket)
 {
-    const int g = grid_for(n);
-    if (dtype == 0)
-        multidot_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, (const double *)p, n, partials, skip);
-    else
-        multidot_f32_kernel<<<g, kThreads, 0, st>>>((const float *)Q, ld, m, (const float *)p, n, partials, skip);
-    reduce(partials, g, m, out, st, skip);
-    count_launches(2);
+    if (dtype == 0) dots_t<double>((const double *)Q, ld, m, (const double *)p, n, partials, out, ticket, skip, st);
+    else dots_t<float>((const float *)Q, ld, m, (const float *)p, n, partials, out, ticket, skip, st);
     return cudaGetLastError();
 }
 
 cudaError_t update_launch(int dtype, const void *Q, int64_t ld, int m, const double *c, void *p,
-                          int64_t n, double *partials, double *norm_out, cudaStream_t st, const int *skip)
+                          int64_t n, double *partials, double *norm_out, cudaStream_t st, const int *skip,
+                          unsigned long long *ticket, LanczosScalars *fin, int fin_i)
 {
-    const int g = grid_for(n);
-    double *part = norm_out ? partials : nullptr;
+    if (fin && (!norm_out || !ticket)) return cudaErrorInvalidValue;
     if (dtype == 0)
-        update_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, m, c, (double *)p, n, part, skip);
+        update_t<double>((const double *)Q, ld, m, c, (double *)p, n, partials, norm_out, ticket, skip, fin, fin_i, st);
     else
-        update_f32_kernel<<<g, kThreads, 0, st>>>((const float *)Q, ld, m, c, (float *)p, n, part, skip);
-    if (norm_out) reduce(partials, g, 1, norm_out, st, skip);
-    count_launches((norm_out ? 2 : 1));
+        update_t<float>((const float *)Q, ld, m, c, (float *)p, n, partials, norm_out, ticket, skip, fin, fin_i, st);
     return cudaGetLastError();
 }
 
 cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const double *div,
                          int div_is_norm2, cudaStream_t st, const int *skip)
 {
-    const int g = grid_for(n);
-    if (dtype == 0)
-        scale_kernel<double><<<g, kThreads, 0, st>>>((const double *)src, (double *)dst, n, div, div_is_norm2, skip);
-    else
-        scale_f32_kernel<<<g, kThreads, 0, st>>>((const float *)src, (float *)dst, n, div, div_is_norm2, skip);
-    count_launches(1);
+    if (dtype == 0) scale_t<double>((const double *)src, (double *)dst, n, div, div_is_norm2, skip, st);
+    else scale_t<float>((const float *)src, (float *)dst, n, div, div_is_norm2, skip, st);
     return cudaGetLastError();
 }
 
 cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, const LanczosScalars *S,
                                  void *p, int64_t n, double *partials, double *out, cudaStream_t st,
-                                 const int *skip)
+                                 const int *skip, unsigned long long *ticket)
 {
-    const int g = grid_for(n);
-    if (dtype == 0)
-        recur_project_kernel<double><<<g, kThreads, 0, st>>>((const double *)Q, ld, i, S, (double *)p, n, partials, skip);
-    else
-        recur_project_kernel<float><<<g, kThreads, 0, st>>>((const float *)Q, ld, i, S, (float *)p, n, partials, skip);
-    reduce(partials, g, i + 1, out, st, skip);
-    count_launches(2);
-    return cudaGetLastError();
-}
-
-cudaError_t finalize_step_launch(LanczosScalars *S, int i, cudaStream_t st)
-{
-    finalize_kernel<<<1, 32, 0, st>>>(S, i);
-    count_launches(1);
+    if (dtype == 0) recur_t<double>((const double *)Q, ld, i, S, (double *)p, n, partials, out, ticket, skip, st);
+    else recur_t<float>((const float *)Q, ld, i, S, (float *)p, n, partials, out, ticket, skip, st);
     return cudaGetLastError();
 }
 
@@ -972,15 +1008,10 @@ cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st)
 }
 
 cudaError_t ritz_launch(int dtype, void *Q, int64_t ld, const int *m_dev, const double *s, int64_t n,
-                        double *partials, double *norm_out, cudaStream_t st)
+                        double *partials, double *norm_out, cudaStream_t st, unsigned long long *ticket)
 {
-    const int g = grid_for(n);
-    if (dtype == 0)
-        ritz_kernel<double><<<g, kThreads, 0, st>>>((double *)Q, ld, m_dev, s, n, partials);
-    else
-        ritz_f32_kernel<<<g, kThreads, 0, st>>>((float *)Q, ld, m_dev, s, n, partials);
-    reduce(partials, g, 1, norm_out, st);
-    count_launches(2);
+    if (dtype == 0) ritz_t<double>((double *)Q, ld, m_dev, s, n, partials, norm_out, ticket, st);
+    else ritz_t<float>((float *)Q, ld, m_dev, s, n, partials, norm_out, ticket, st);
     return cudaGetLastError();
 }
 
@@ -1010,12 +1041,15 @@ cudaError_t convert_launch(int dst_dtype, void *dst, int src_dtype, const void *
 }
 
 cudaError_t residual_launch(const double *a, const double *b, const double *lambda, double *dst,
-                            int64_t n, double *partials, double *norm_out, cudaStream_t st)
+                            int64_t n, double *partials, double *norm_out, cudaStream_t st,
+                            unsigned long long *ticket)
 {
-    const int g = grid_for(n);
-    residual_kernel<<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials);
-    reduce(partials, g, 1, norm_out, st);
-    count_launches(2);
+    const bool pk = packable<double>({a, b, dst}, 0);
+    const int g = pk ? wave_grid<residual_kernel<2>>(pack_units<double>(n, pk)) : wave_grid<residual_kernel<1>>(n);
+    if (pk) residual_kernel<2><<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials, norm_out, ticket);
+    else residual_kernel<1><<<g, kThreads, 0, st>>>(a, b, lambda, dst, n, partials, norm_out, ticket);
+    count_launches(1);
+    if (!ticket) reduce(partials, g, 1, norm_out, st);
     return cudaGetLastError();
 }
 
