@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--batch", action="store_true",
                     help="4096-problem mean-field workload: solves/s and per-solve latency (own JSON line)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--big", action="store_true",
+                    help="Omega=32, N=16 (dim 6.0e8): time-to-E0 of FP64, mixed and mixed+learned start")
     ap.add_argument("--warm", action="store_true",
                     help="Omega=30 workload: FP64 random start vs mixed + learned warm start (own JSON line)")
     ap.add_argument("--train-problems", type=int, default=240)
@@ -492,22 +494,49 @@ def run_warm(args):
     """Omega=30, N=15 (dim 1.55e8, seed 2): time-to-E0 and Lanczos iterations of
     plain FP64 Lanczos from a random start vs the mixed form from the learned
     warm start (and from a random start), same tolerance."""
+    return run_forms(args, "omega30_n15_sepnoise_s2", "warm_start")
+
+
+def run_big(args):
+    """Omega=32, N=16 (dim 6.0e8, seed 3), the largest single solve: the same
+    three forms, each on its own (their windows do not fit on the device
+    together), with the in-situ H*x roofline of both precisions."""
+    return run_forms(args, "omega32_n16_constnoise_s3", "largest_single_solve")
+
+
+def run_forms(args, workload, tag):
+    """One solver per form, created, warmed up (first-touch of the window and
+    FP64 vectors), timed over --steps solves, and closed before the next form."""
     import torch
     import paper_2001_01978_gb300 as pd
     torch.cuda.set_device(0)
     ws, train_s, l0, l1, rows = train_warm_start(args.train_problems, args.train_steps)
-    omega, n, e, G = pd_inputs.workload("omega30_n15_sepnoise_s2")
+    omega, n, e, G = pd_inputs.workload(workload)
+    dim = math.comb(omega, n)
+    nnz = dim * n * (omega - n)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    tuned = {}
+    if not args.no_autotune:
+        for pname, prec in (("fp32", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
+            best, _ = pd.pairdiag_autotune(omega, n, e, G, prec, reps=3)
+            tuned[pname] = best
     forms = [("fp64_random", pd.PD_PREC_FP64, pd.PD_START_RANDOM),
              ("mixed_random", pd.PD_PREC_MIXED, pd.PD_START_RANDOM),
              ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP)]
-    out = {}
+    peak, peak_kind = measured_peaks()
+    out, roof = {}, {}
+    clocks = ClockSampler(0)
     for name, prec, start in forms:
         with pd.Solver(omega, n, e, G, precision=prec, start=start, window=args.window, seed=1) as s:
             pd.pairdiag_set_stream(s.h, stream)
             if start == pd.PD_START_MLP:
                 ws.attach(s.h)
+            for _ in range(args.warmup):
+                flush.fill_(1.0)
+                pd.pairdiag_ground_state_dev(s.h, args.tol, None)
+            pd.pairdiag_set_profiling(s.h, True)
+            pd.pairdiag_get_profile(s.h)                  # clear
             times, r = [], None
             for i in range(max(1, args.steps)):
                 flush.fill_(1.0)
@@ -517,17 +546,32 @@ def run_warm(args):
                 ev1.record(stream)
                 ev1.synchronize()
                 times.append(ev0.elapsed_time(ev1))
+            pkey = "fp64" if prec == pd.PD_PREC_FP64 else "fp32"
+            cnt, ms = pd.pairdiag_get_profile(s.h, pd.PD_PREC_FP64 if pkey == "fp64" else pd.PD_PREC_MIXED)
+            pd.pairdiag_set_profiling(s.h, False)
+            if cnt and pkey not in roof:
+                es = 8 if pkey == "fp64" else 4
+                alg = nnz * es + 2 * dim * es
+                avg_s = ms / cnt * 1e-3
+                roof[pkey] = {"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / avg_s / 1e9 / peak, "peak_kind": peak_kind,
+                              "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
+                              "hx_nnz_per_s": nnz / avg_s, "launches": cnt}
         out[name] = {"time_to_e0_ms": statistics.median(times), "iterations": r["iterations"],
-                     "hx_products": r["hx_products"], "e0": r["e0"], "rel_residual": r["rel_residual"],
-                     "status": r["status"]}
+                     "iterations_fp32": r["iterations_fp32"], "hx_products": r["hx_products"],
+                     "nnz_per_s": r["hx_products"] * nnz / (statistics.median(times) * 1e-3),
+                     "e0": r["e0"], "rel_residual": r["rel_residual"], "status": r["status"]}
+    clk = clocks.stop()
     ref = out["fp64_random"]["e0"]
     for v in out.values():
         v["e0_rel_diff_vs_fp64"] = abs(v["e0"] - ref) / abs(ref)
-    print(json.dumps({"warm_start": True, "workload": "omega30_n15_sepnoise_s2", "dim": math.comb(omega, n),
-                      "tol": args.tol, "window": args.window, "steps": args.steps,
+    print(json.dumps({tag: True, "workload": workload, "omega": omega, "n_pairs": n, "dim": dim,
+                      "nnz_offdiag_per_hx": nnz, "tol": args.tol, "window": args.window,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "l2": "flushed between solves (512 MB write)",
                       "training": {"problems": args.train_problems, "rows": rows, "seconds": train_s,
                                    "loss_first": l0, "loss_last": l1},
-                      "forms": out,
+                      "autotune": tuned, "forms": out, "hx_roofline": roof, "clocks": clk,
                       "speedup_mixed_mlp_vs_fp64_random": out["fp64_random"]["time_to_e0_ms"] / out["mixed_mlp"]["time_to_e0_ms"]}))
     ws.close()
     return 0
@@ -591,6 +635,8 @@ def main():
         return run_batch(args)
     if args.warm:
         return run_warm(args)
+    if args.big:
+        return run_big(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

@@ -173,3 +173,55 @@ def test_omega30_mixed_temple_bound():
     assert abs(lam - r["e0"]) <= 1e-12 * abs(lam)
     gap = max(r["gap_estimate"], 1e-3)
     assert res * res / gap <= 1e-8 * abs(lam)
+
+
+# ------------------------------------------------- largest single solves ----
+def test_omega32_constant_g_twin_richardson():
+    """Omega=32, N=16 (dim 6.0e8): the levels of the Omega=32 workload with its
+    noise switched off (G = -0.4 exactly).  Constant pairing is solvable by the
+    Richardson equations at any size, so the mixed form's E0 is pinned to 1e-8
+    relative without any CPU diagonalisation."""
+    omega, n, e, _ = pd_inputs.workload("omega32_n16_constnoise_s3")
+    G = np.full((omega, omega), -0.4)
+    ref = richardson.ground_energy(e, -0.4, n)
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=20) as s:
+        r = pd.pairdiag_ground_state_dev(s.h, 1e-9, None)
+    assert r["status"] == pd.PD_OK
+    assert abs(r["e0"] - ref) <= 1e-8 * abs(ref)
+
+
+def test_omega32_mixed_temple_bound():
+    """Omega=32, N=16 separable-plus-constant noise (seed 3), mixed form: the FP64
+    Rayleigh quotient of the returned vector and its residual bound the error
+    by r^2/gap (Kato-Temple); the FP64 H*x used here is checked row by row
+    against the oracle at this size in test_gpu_kernels."""
+    omega, n, e, G = pd_inputs.workload("omega32_n16_constnoise_s3")
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=20) as s:
+        v = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+        r = pd.pairdiag_ground_state_dev(s.h, 1e-9, v)
+        assert r["status"] == pd.PD_OK
+        w = torch.empty_like(v)
+        pd.pairdiag_hx_dev(s.h, pd.PD_PREC_FP64, v, w)
+        lam = float(v @ w) / float(v @ v)
+        res = float(torch.linalg.vector_norm(w - lam * v)) / float(torch.linalg.vector_norm(v))
+        del v, w
+    assert abs(lam - r["e0"]) <= 1e-12 * abs(lam)
+    gap = max(r["gap_estimate"], 1e-3)
+    assert res * res / gap <= 1e-8 * abs(lam)
+
+
+@pytest.mark.parametrize("row", read_golden("table3_richardson_g04.txt")[3:4])
+def test_table3_large_rows_mixed(row):
+    """Table 3 row C(34,10) = 1.3e8, mixed form with FP64 continuation to a 1e-9
+    residual: the PairDiag column (G rounded to single precision) to its 7
+    printed decimals, and the Richardson energy of the same rounded G to 1e-10
+    relative."""
+    omega, n = int(row[0]), int(row[1])
+    e, G = pd_inputs.picket_fence(omega, -0.4, g_float32=True)
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=20) as s:
+        assert s.dim == int(row[2])
+        r = pd.pairdiag_ground_state_dev(s.h, 1e-9, None)
+    assert r["status"] == pd.PD_OK
+    assert abs(r["e0"] - float(row[3])) <= 0.5e-7 + 1e-9
+    ref = richardson.ground_energy(e, float(np.float32(-0.4)), n)
+    assert abs(r["e0"] - ref) <= 1e-10 * abs(ref)

@@ -271,3 +271,16 @@ def test_richardson_one_pair_secular_equation():
     for g in (-0.3, -1.5):
         ref = np.linalg.eigvalsh(np.diag(2 * e) + g * np.ones((5, 5)))[0]
         assert abs(richardson.ground_energy(e, g, 1) - ref) < 1e-12
+
+
+@pytest.mark.parametrize("seed,g", [(3, -0.4), (4, -0.4), (5, -1.5), (6, -0.05)])
+def test_richardson_random_levels_vs_dense(seed, g):
+    """Constant G with unsorted levels drawn uniform in [-10, 10] (the level
+    distribution of the Omega=32, N=16 workload, whose constant-G twin is a
+    large-size GPU pin): the Richardson energy equals the lowest eigenvalue of the
+    dense matrix of Eq. 2 (a library eigensolve), for weak and strong pairing."""
+    omega, n = 12, 6
+    e = np.random.default_rng(seed).uniform(-10.0, 10.0, omega)
+    G = np.full((omega, omega), g)
+    ref = np.linalg.eigvalsh(oracle.dense_matrix(omega, n, e, G))[0]
+    assert abs(richardson.ground_energy(e, g, n) - ref) <= 1e-11 * max(1.0, abs(ref))
