@@ -191,11 +191,15 @@ int build_tables(pairdiag *h)
     // admissible k (pairs in the low orbits)
     const int kmin = std::max(0, N - H), kmax = std::min(N, L);
     int64_t nblocks = 0;
-    int max_block = 0, max_hh = 0;
+    int max_block = 0, max_hh = 0, max_stage = 0;
     for (int k = kmin; k <= kmax; ++k) {
-        nblocks += (int64_t)host_binom(H, N - k);
+        const int ph = N - k;
+        nblocks += (int64_t)host_binom(H, ph);
         max_block = std::max(max_block, (int)host_binom(L, k));
-        max_hh = std::max(max_hh, (N - k) * (H - (N - k)));
+        max_hh = std::max(max_hh, ph * (H - ph));
+        const int64_t up = (k < L && ph > 0) ? ph * (int64_t)host_binom(L, k + 1) : 0;
+        const int64_t dn = (k > 0 && H - ph > 0) ? (H - ph) * (int64_t)host_binom(L, k - 1) : 0;
+        max_stage = (int)std::max<int64_t>(max_stage, up + dn);
     }
     if (nblocks > (int64_t)1 << 31) return fail(PD_ENOTSUP, "too many basis blocks (%lld)", (long long)nblocks);
     std::vector<uint64_t> hw;
@@ -239,6 +243,7 @@ int build_tables(pairdiag *h)
     B.nblocks = (int64_t)hw.size();
     B.max_block = max_block;
     B.max_hh = max_hh;
+    B.max_stage = max_stage;
     B.variant = h->opt.hx_variant;
     B.blk_h = h->d_blk_h; B.blk_base = h->d_blk_base;
     B.lowword = h->d_lowword; B.rankL = h->d_rankL; B.binom = h->d_binom;

@@ -79,12 +79,11 @@ __device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
     return s;
 }
 
-// One basis block (high word h, first index base) of y = H x.  x and y point at
-// the problem's own vector; sG/sd/sRank hold its G, d and rank table.  Called
-// by every thread of the CTA (it contains barriers).
-// x^T y over one basis block (this CTA's rows; y as stored), into *out (thread 0)
+// x^T y over this warp's rows of one basis block (y as stored) into sw[warp]
+// (lane 0).  No barrier: thread 0 adds the warp sums in warp order after the
+// barrier that opens the next block (block_sum_deferred).
 template <typename T, typename A, int R>
-__device__ __forceinline__ void block_dot(const A *acc, const T *sx, int nk, double *out, double *sred)
+__device__ __forceinline__ void warp_dot(const A *acc, const T *sx, int nk, double *sw)
 {
     DotAcc<T> d;
 #pragma unroll
@@ -92,8 +91,18 @@ __device__ __forceinline__ void block_dot(const A *acc, const T *sx, int nk, dou
         const int r = threadIdx.x + i * kThreads;
         if (r < nk) d.add(sx[r], T(acc[i]));
     }
-    const double s = block_reduce(d, sred);
-    if (threadIdx.x == 0) *out = s;
+    const double s = warp_reduce(d);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+}
+
+// Thread 0, after a barrier: the previous block's warp sums into blk_part[prev]
+__device__ __forceinline__ void block_sum_deferred(double *blk_part, long long prev, const double *sw)
+{
+    if (!blk_part || prev < 0) return;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += sw[w];
+    blk_part[prev] = s;
 }
 
 // End of a persistent H*x launch, called by every CTA: the last one to arrive
@@ -112,6 +121,10 @@ __device__ __forceinline__ void hx_finish(Tickets *tk, int64_t nblocks, const do
     if (threadIdx.x == 0) *dot_out = s;
 }
 
+// One basis block (high word h, first index base) of y = H x.  x and y point at
+// the problem's own vector; sG/sd/sRank hold its G, d and rank table.  Called
+// by every thread of the CTA (it contains barriers).  swdot (nullable): the
+// block's x^T y per warp (warp_dot).
 template <typename T, typename A, int R>
 __device__ __forceinline__ void hx_block(const int omega, const int L, const int H, const int N,
                                          const uint64_t h, const uint64_t base,
@@ -119,7 +132,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
                                          const uint64_t *__restrict__ binom,
                                          const A *sG, const A *sd, const uint16_t *sRank, T *sx, T *sxn,
                                          HHop<A> *sHH, uint64_t *sMX, const T *__restrict__ x,
-                                         T *__restrict__ y, double *blk_dot, double *sred)
+                                         T *__restrict__ y, double *swdot)
 {
     const int tid = threadIdx.x;
     const uint32_t maskL = (1u << L) - 1u;
@@ -253,7 +266,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         const int r = tid + i * kThreads;
         if (r < nk) y[base + r] = T(acc[i]);
     }
-    if (blk_dot) block_dot<T, A, R>(acc, sx, nk, blk_dot, sred);
+    if (swdot) warp_dot<T, A, R>(acc, sx, nk, swdot);
 }
 
 template <typename T, typename A, int R>
@@ -264,8 +277,9 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 {
     if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_next;
+    __shared__ long long s_next[2];
     __shared__ double sred[kThreads / 32];
+    __shared__ double swdot[kThreads / 32];
     const int omega = B.omega, L = B.L, H = B.H, N = B.n;
     const Layout lay = layout<T, A>(omega, L, H, B.max_block, B.max_hh);
     A *sG = reinterpret_cast<A *>(smem + lay.G);
@@ -281,15 +295,22 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
     for (int i = tid; i < (1 << L); i += kThreads) sRank[i] = B.rankL[i];
 
-    for (;;) {
+    // the next block index is taken one block ahead (slot it ^ 1), so one
+    // barrier per block both frees shared memory and publishes the index
+    if (tid == 0) s_next[0] = (long long)atomicAdd(&tk->hx_next, 1ull);
+    long long prev = -1;
+    for (int it = 0;; it ^= 1) {
         __syncthreads();                          // smem of the previous block is free
-        if (tid == 0) s_next = (long long)atomicAdd(&tk->hx_next, 1ull);
-        __syncthreads();
-        const long long b = s_next;
+        const long long b = s_next[it];
+        if (tid == 0) {
+            block_sum_deferred(blk_part, prev, swdot);
+            if (b < B.nblocks) s_next[it ^ 1] = (long long)atomicAdd(&tk->hx_next, 1ull);
+        }
         if (b >= B.nblocks) break;
 
         hx_block<T, A, R>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
-                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? blk_part + b : nullptr, sred);
+                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? swdot : nullptr);
+        prev = b;
     }
     hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
@@ -340,29 +361,31 @@ hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__res
         }
         hx_block<T, A, R>(dsc.omega, dsc.L, dsc.omega - dsc.L, dsc.n, __ldg(BB.blk_h + b), __ldg(BB.blk_base + b),
                           BB.lowword_all + dsc.tab_off, BB.binom, sG, sd, sRank, sx, sxn, sHH, sMX,
-                          x + dsc.vec_off, y + dsc.vec_off, nullptr, nullptr);
+                          x + dsc.vec_off, y + dsc.vec_off, nullptr);
     }
 }
 
 // ---- variant 2: every neighbouring block of the high<->low hops staged at once --
 struct Layout2 {
-    size_t gl, gs, ge, d, rank, x, xn, ud, hh, occ, emp, total;
+    size_t g, gs, ge, d, rank, low, bin, x, xn, hh, occ, emp, total;
 };
 
 template <typename T, typename A>
-__host__ __device__ inline Layout2 layout2(int omega, int L, int H, int max_block, int max_hh)
+__host__ __device__ inline Layout2 layout2(int omega, int L, int H, int N, int max_block, int max_hh,
+                                          int max_stage)
 {
     Layout2 s;
     size_t off = 0;
     const int h1 = H > 0 ? H : 1;
-    s.gl = off;   off = align16(off + sizeof(A) * L * L);
+    s.g = off;    off = align16(off + sizeof(A) * omega * omega);
     s.gs = off;   off = align16(off + sizeof(A) * h1 * L);
     s.ge = off;   off = align16(off + sizeof(A) * h1 * L);
     s.d = off;    off = align16(off + sizeof(A) * omega);
     s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
+    s.low = off;  off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
+    s.bin = off;  off = align16(off + sizeof(uint64_t) * h1 * (N + 1));
     s.x = off;    off = align16(off + sizeof(T) * max_block);
-    s.xn = off;   off = align16(off + sizeof(T) * (size_t)h1 * max_block);
-    s.ud = off;   off = align16(off + sizeof(uint16_t) * (size_t)L * max_block);
+    s.xn = off;   off = align16(off + sizeof(T) * (size_t)(max_stage > 0 ? max_stage : 1));
     s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
     s.occ = off;  off = align16(off + sizeof(uint64_t) * h1);
     s.emp = off;  off = align16(off + sizeof(uint64_t) * h1);
@@ -370,97 +393,176 @@ __host__ __device__ inline Layout2 layout2(int omega, int L, int H, int max_bloc
     return s;
 }
 
+// block_base with the binomials of the high orbits in shared memory:
+// sBin[p * (N + 1) + m] = C(L + p, m)
+__device__ __forceinline__ uint64_t block_base_s(uint64_t h, int N, const uint64_t *sBin)
+{
+    int ord = N - __popcll(h);
+    uint64_t s = 0;
+    while (h) {
+        const int p = __ffsll((long long)h) - 1;
+        h &= h - 1;
+        ++ord;
+        s += sBin[p * (N + 1) + ord];
+    }
+    return s;
+}
+
+// asynchronous copy of one 4- or 8-byte element global -> shared (no register
+// round trip, so a thread issues all its copies before any has landed)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element of 4 or 8 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Same product as hx_kernel.  Differences: all ph blocks h - o (k+1 low pairs)
-// and all H-ph blocks h + e (k-1) are staged together behind one barrier; each
-// row's neighbour ranks rank(l + e) and rank(l - o) are computed once per block
-// and kept packed (rank << 4 | orbit) in shared memory; the coefficients of the
+// and all H-ph blocks h + e (k-1) are staged together; the coefficients of the
 // high<->low hops are laid out per staged block (G_{e, L+t} for block h - t at
-// row t of sGS, G_{L+t, o} for block h + t in sGE), so the innermost loop runs
-// over the staged blocks with one coefficient load, one gather and one FMA.
+// row t of sGS, G_{L+t, o} for block h + t in sGE), so for each row and low
+// orbit the innermost loop runs over the staged blocks with one coefficient
+// load, one gather and one FMA.
+//
+// Latency: G, d, the rank and low-word tables and the binomials of the high
+// orbits live in shared memory for the whole launch, so the per-block tables
+// need no global loads; the block's own x and its neighbours arrive through
+// cp.async, issued before the table setup and before the low->low and
+// high->high hops respectively, so their latency overlaps that work; thread 0
+// takes the next block index and copies its (h, base) into shared memory one
+// block ahead.  FP32: at most 40 registers, so that six CTAs fit an SM when
+// shared memory allows.
 template <typename T, typename A, int R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4)
 hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
            const T *__restrict__ x, T *__restrict__ y, Tickets *tk, const int *__restrict__ skip,
            double *blk_part, double *dot_out)
 {
     if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_next;
+    __shared__ int s_idx[2];
+    __shared__ __align__(8) uint64_t s_h[2], s_base[2];
     __shared__ double sred[kThreads / 32];
-    const int omega = B.omega, L = B.L, H = B.H, N = B.n, MB = B.max_block;
-    const Layout2 lay = layout2<T, A>(omega, L, H, MB, B.max_hh);
-    A *sGL = reinterpret_cast<A *>(smem + lay.gl);
+    __shared__ double swdot[kThreads / 32];
+    const int omega = B.omega, L = B.L, H = B.H, N = B.n;
+    const Layout2 lay = layout2<T, A>(omega, L, H, N, B.max_block, B.max_hh, B.max_stage);
+    A *sG = reinterpret_cast<A *>(smem + lay.g);
     A *sGS = reinterpret_cast<A *>(smem + lay.gs);
     A *sGE = reinterpret_cast<A *>(smem + lay.ge);
     A *sd = reinterpret_cast<A *>(smem + lay.d);
     uint16_t *sRank = reinterpret_cast<uint16_t *>(smem + lay.rank);
+    uint16_t *sLow = reinterpret_cast<uint16_t *>(smem + lay.low);
+    uint64_t *sBin = reinterpret_cast<uint64_t *>(smem + lay.bin);
     T *sx = reinterpret_cast<T *>(smem + lay.x);
     T *sxn = reinterpret_cast<T *>(smem + lay.xn);
-    uint16_t *sUD = reinterpret_cast<uint16_t *>(smem + lay.ud);
     HHop<A> *sHH = reinterpret_cast<HHop<A> *>(smem + lay.hh);
     uint64_t *sOccB = reinterpret_cast<uint64_t *>(smem + lay.occ);
     uint64_t *sEmpB = reinterpret_cast<uint64_t *>(smem + lay.emp);
     const int tid = threadIdx.x;
 
-    for (int i = tid; i < L * L; i += kThreads) sGL[i] = Gg[(i / L) * omega + (i % L)];
+    for (int i = tid; i < omega * omega; i += kThreads) sG[i] = Gg[i];
     for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
-    for (int i = tid; i < (1 << L); i += kThreads) sRank[i] = B.rankL[i];
+    for (int i = tid; i < (1 << L); i += kThreads) {
+        sRank[i] = B.rankL[i];
+        sLow[i] = B.lowword[i];
+    }
+    for (int i = tid; i < (H > 0 ? H : 1) * (N + 1); i += kThreads) {
+        const int p = i / (N + 1), m = i - p * (N + 1);
+        sBin[i] = __ldg(B.binom + (L + p) * kBinomStride + m);
+    }
     const uint32_t maskL = (1u << L) - 1u;
     const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
 
-    for (;;) {
-        __syncthreads();                          // smem of the previous block is free
-        if (tid == 0) s_next = (long long)atomicAdd(&tk->hx_next, 1ull);
-        __syncthreads();
-        const long long b = s_next;
-        if (b >= B.nblocks) break;
+    // block schedule: slot it holds (index, h, base) of the block of iteration
+    // it.  Thread 0 holds the index of the next block in nb1; during the
+    // current block it copies that block's (h, base) into slot it ^ 1 with
+    // cp.async (completed by its cp.async waits below) and takes the index
+    // after it from the counter, so neither latency delays a block.
+    // (Block counts are below 2^31: build_tables rejects more blocks.)
+    const int nblocks = (int)B.nblocks;
+    int nb1 = 0;
+    if (tid == 0) {
+        const int b0 = (int)atomicAdd(&tk->hx_next, 1ull);
+        s_idx[0] = b0;
+        if (b0 < nblocks) {
+            s_h[0] = __ldg(B.blk_h + b0);
+            s_base[0] = __ldg(B.blk_base + b0);
+            nb1 = (int)atomicAdd(&tk->hx_next, 1ull);
+        }
+    }
+    long long prev = -1;
+    for (int it = 0;; it ^= 1) {
+        __syncthreads();                          // smem of the previous block is free; slot it visible
+        const int b = s_idx[it];
+        int nb2 = 0;
+        if (tid == 0) {
+            block_sum_deferred(blk_part, prev, swdot);
+            if (b < nblocks && nb1 < nblocks) {
+                cp_async_elem(&s_h[it ^ 1], B.blk_h + nb1);
+                cp_async_elem(&s_base[it ^ 1], B.blk_base + nb1);
+                nb2 = (int)atomicAdd(&tk->hx_next, 1ull);
+            }
+        }
+        if (b >= nblocks) break;
 
-        const uint64_t h = __ldg(B.blk_h + b);
-        const uint64_t base = __ldg(B.blk_base + b);
+        const uint64_t h = s_h[it];
+        const uint64_t base = s_base[it];
         const int ph = __popcll(h);
         const int k = N - ph;
-        const int nk = (int)__ldg(B.binom + L * kBinomStride + k);
-        const uint16_t *lw = B.lowword + B.lo_off[k];
         const int nemp = H - ph;
         const int nhh = ph * nemp;
-        const int n_up = (k < L) ? (int)__ldg(B.binom + L * kBinomStride + k + 1) : 0;
-        const int n_dn = (k > 0) ? (int)__ldg(B.binom + L * kBinomStride + k - 1) : 0;
+        // block sizes C(L, k), C(L, k+1), C(L, k-1) from row p = 0 of sBin
+        // (k + 1 <= N whenever a block h - o exists, i.e. ph > 0)
+        const int nk = (int)sBin[k];
+        const int n_up = (k < L && ph > 0) ? (int)sBin[k + 1] : 0;
+        const int n_dn = (k > 0 && nemp > 0) ? (int)sBin[k - 1] : 0;
+        const uint16_t *lw = sLow + B.lo_off[k];
         T *sxd = sxn + ph * n_up;                 // staged blocks h + e start here
+
+        for (int r = tid; r < nk; r += kThreads) cp_async_elem(sx + r, x + base + r);
+        cp_async_commit();
 
         for (int t = tid; t < nhh; t += kThreads) {
             const int a = t / nemp, c = t - a * nemp;
             const int o = nth_set_bit(h, a);
             const int q = nth_set_bit(~h & maskH, c);
-            sHH[t].base = block_base(h ^ (1ull << o) ^ (1ull << q), L, N, B.binom);
-            sHH[t].g = Gg[(L + q) * omega + (L + o)];
+            sHH[t].base = block_base_s(h ^ (1ull << o) ^ (1ull << q), N, sBin);
+            sHH[t].g = sG[(L + q) * omega + (L + o)];
         }
         for (int t = tid; t < H; t += kThreads) {
             const uint64_t bit = 1ull << t;
             if (h & bit) {
                 const int j = __popcll(h & (bit - 1));
-                sOccB[j] = n_up ? block_base(h ^ bit, L, N, B.binom) : 0;
-                for (int e = 0; e < L; ++e) sGS[j * L + e] = Gg[e * omega + L + t];
+                sOccB[j] = n_up ? block_base_s(h ^ bit, N, sBin) : 0;
+                for (int e = 0; e < L; ++e) sGS[j * L + e] = sG[e * omega + L + t];
             } else {
                 const int j = __popcll(~h & maskH & (bit - 1));
-                sEmpB[j] = n_dn ? block_base(h | bit, L, N, B.binom) : 0;
-                for (int o = 0; o < L; ++o) sGE[j * L + o] = Gg[(L + t) * omega + o];
+                sEmpB[j] = n_dn ? block_base_s(h | bit, N, sBin) : 0;
+                for (int o = 0; o < L; ++o) sGE[j * L + o] = sG[(L + t) * omega + o];
             }
         }
-        for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
-        __syncthreads();                          // slot bases visible
+        cp_async_wait_all();
+        __syncthreads();                          // own block, hop tables and slot bases visible
 
         if (n_up)
             for (int j = 0; j < ph; ++j) {
                 const T *src = x + sOccB[j];
                 T *dst = sxn + j * n_up;
-                for (int r = tid; r < n_up; r += kThreads) dst[r] = src[r];
+                for (int r = tid; r < n_up; r += kThreads) cp_async_elem(dst + r, src + r);
             }
         if (n_dn)
             for (int j = 0; j < nemp; ++j) {
                 const T *src = x + sEmpB[j];
                 T *dst = sxd + j * n_dn;
-                for (int r = tid; r < n_dn; r += kThreads) dst[r] = src[r];
+                for (int r = tid; r < n_dn; r += kThreads) cp_async_elem(dst + r, src + r);
             }
+        cp_async_commit();
 
         A Dh = A(0);
         for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
@@ -478,17 +580,6 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
                 A D = A(0);
                 for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
                 acc[i] = (D + Dh) * A(sx[r]);
-                // neighbour ranks of this row: up (l + e) then down (l - o); only
-                // this thread reads them back
-                int slot = 0;
-                for (uint32_t w = ~l & maskL; w; w &= w - 1, ++slot) {
-                    const int e = __ffs(w) - 1;
-                    sUD[slot * MB + r] = (uint16_t)((sRank[l | (1u << e)] << 4) | e);
-                }
-                for (uint32_t w = l; w; w &= w - 1, ++slot) {
-                    const int o = __ffs(w) - 1;
-                    sUD[slot * MB + r] = (uint16_t)((sRank[l ^ (1u << o)] << 4) | o);
-                }
             }
         }
 
@@ -504,12 +595,12 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
                         const int o = __ffs(occ) - 1;
                         occ &= occ - 1;
                         const uint32_t lo = l ^ (1u << o);
-                        const A *gcol = sGL + o;
+                        const A *gcol = sG + o;
                         uint32_t emp = ~l & maskL;
                         for (int v = 0; v < L - k; ++v) {
                             const int q = __ffs(emp) - 1;
                             emp &= emp - 1;
-                            a += gcol[q * L] * A(sx[sRank[lo | (1u << q)]]);
+                            a += gcol[q * omega] * A(sx[sRank[lo | (1u << q)]]);
                         }
                     }
                     acc[i] = a;
@@ -527,19 +618,22 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
                 if (r < nk) acc[i] += g * A(__ldg(xb + r));
             }
         }
+        cp_async_wait_all();
         __syncthreads();                          // staged neighbour blocks visible
 
-        // high -> low: pair from occupied high orbit L+t to empty low orbit e
+        // high -> low: pair from occupied high orbit L+t to empty low orbit e;
+        // the target offset rank(l + e) is the same in every staged block
         if (n_up) {
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const int r = tid + i * kThreads;
                 if (r < nk) {
+                    const uint32_t l = lr[i];
                     A a = acc[i];
-                    for (int v = 0; v < L - k; ++v) {
-                        const uint32_t pk = sUD[v * MB + r];
-                        const A *g = sGS + (pk & 15u);
-                        const T *xp = sxn + (pk >> 4);
+                    for (uint32_t w = ~l & maskL; w; w &= w - 1) {
+                        const int e = __ffs(w) - 1;
+                        const A *g = sGS + e;
+                        const T *xp = sxn + sRank[l | (1u << e)];
                         for (int j = 0; j < ph; ++j) a += g[j * L] * A(xp[j * n_up]);
                     }
                     acc[i] = a;
@@ -552,11 +646,12 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
             for (int i = 0; i < R; ++i) {
                 const int r = tid + i * kThreads;
                 if (r < nk) {
+                    const uint32_t l = lr[i];
                     A a = acc[i];
-                    for (int u = 0; u < k; ++u) {
-                        const uint32_t pk = sUD[(L - k + u) * MB + r];
-                        const A *g = sGE + (pk & 15u);
-                        const T *xp = sxd + (pk >> 4);
+                    for (uint32_t w = l; w; w &= w - 1) {
+                        const int o = __ffs(w) - 1;
+                        const A *g = sGE + o;
+                        const T *xp = sxd + sRank[l ^ (1u << o)];
                         for (int j = 0; j < nemp; ++j) a += g[j * L] * A(xp[j * n_dn]);
                     }
                     acc[i] = a;
@@ -569,21 +664,26 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
             const int r = tid + i * kThreads;
             if (r < nk) y[base + r] = T(acc[i]);
         }
-        if (blk_part) block_dot<T, A, R>(acc, sx, nk, blk_part + b, sred);
+        if (blk_part) warp_dot<T, A, R>(acc, sx, nk, swdot);
+        prev = b;
+        if (tid == 0) {                           // publish the next block (read after the barrier)
+            s_idx[it ^ 1] = nb1;
+            nb1 = nb2;
+        }
     }
     hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
 
 constexpr size_t kSmemLimit = 200 * 1024;
 
-// Variant 2 only on request (and when its shared memory fits): measured on
-// GB300 it is slower than variant 1 (0.40 vs 0.30 ms at Omega=24, 157 vs 99 ms at
-// Omega=32 in FP32) because its shared-memory footprint leaves 1-2 CTAs per SM.
+// Variant 2 only on request (the autotuner's choice, or the caller's) and when
+// its shared memory fits; which variant is faster depends on the problem and
+// the block split (at Omega=24 variant 2 with L=11 in FP32, at Omega=32 variant 1).
 template <typename T, typename A>
 bool use_v2(const Blocks &B)
 {
     if (B.variant != 2) return false;
-    return layout2<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total <= kSmemLimit;
+    return layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total <= kSmemLimit;
 }
 
 template <typename T, typename A, int R>
@@ -595,7 +695,7 @@ const void *kernel_fn(const Blocks &B)
 template <typename T, typename A>
 size_t kernel_smem(const Blocks &B)
 {
-    return use_v2<T, A>(B) ? layout2<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total
+    return use_v2<T, A>(B) ? layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total
                            : layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
 }
 

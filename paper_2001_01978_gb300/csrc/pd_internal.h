@@ -55,6 +55,8 @@ struct Blocks {
     int64_t nblocks;
     int max_block;                   // max_k C(L, k) over admissible k
     int max_hh;                      // max over blocks of the number of high->high hops
+    int max_stage;                   // max over blocks of the elements of all neighbour blocks
+                                     // (ph C(L, k+1) + (H - ph) C(L, k-1))
     const uint64_t *blk_h;           // [nblocks] high words, ascending
     const uint64_t *blk_base;        // [nblocks] index of the block's first state
     const uint16_t *lowword;         // [2^L] L-bit words grouped by popcount, ascending
@@ -124,11 +126,28 @@ __device__ __forceinline__ void ff_add(float &ah, float &al, float bh, float bl)
     ah = h;
 }
 
+// warp-wide sum of one double per lane; result valid in lane 0
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// warp-wide float-float sum; result valid in lane 0
+__device__ __forceinline__ void warp_sum_ff(float &hi, float &lo)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, oh, ol);
+    }
+}
+
 // block-wide sum of one double per thread; result valid in thread 0.
 // sh: at least blockDim.x / 32 doubles of shared memory.
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    v = warp_sum(v);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
     if (lane == 0) sh[w] = v;
@@ -143,11 +162,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // the whole reduction tree stays on the FP32 pipes.  sh: blockDim.x / 16 floats.
 __device__ __forceinline__ double block_sum_ff(float hi, float lo, float *sh)
 {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
-        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
-        ff_add(hi, lo, oh, ol);
-    }
+    warp_sum_ff(hi, lo);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
     if (lane == 0) { sh[2 * w] = hi; sh[2 * w + 1] = lo; }
@@ -180,6 +195,14 @@ __device__ __forceinline__ double block_reduce(const DotAcc<double> &a, double *
 __device__ __forceinline__ double block_reduce(const DotAcc<float> &a, double *sh)
 {
     return block_sum_ff(a.hi, a.lo, reinterpret_cast<float *>(sh));
+}
+// warp-wide sum of the accumulators (lane 0)
+__device__ __forceinline__ double warp_reduce(const DotAcc<double> &a) { return warp_sum(a.get()); }
+__device__ __forceinline__ double warp_reduce(const DotAcc<float> &a)
+{
+    float hi = a.hi, lo = a.lo;
+    warp_sum_ff(hi, lo);
+    return (double)hi + (double)lo;
 }
 
 // Called by every thread of every CTA after thread 0 has written the CTA's
