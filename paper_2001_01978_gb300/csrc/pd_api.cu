@@ -387,7 +387,7 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
             // the caller refines in FP64
             history.push_back(cs.rel);
             const size_t nh = history.size();
-            if (dtype == 1 && nh >= 4 && history[nh - 1] > 0.7 * history[nh - 4]) return PD_OK;
+            if (dtype == 1 && nh >= 4 && fp32_stalled(history[nh - 1], history[nh - 4], tol)) return PD_OK;
         }
         for (int i = 1; i < m; ++i) {
             PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));

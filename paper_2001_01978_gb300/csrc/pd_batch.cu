@@ -164,9 +164,11 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
             run += host_binom(L, n - __builtin_popcountll(w));
         }
         if ((int64_t)run != dim) return fail(PD_ECUDA, "batch: blocks do not cover problem %d", p);
-        // chunks: at most 32 per problem, at least ~1024 elements each
+        // chunks: at most 32 per problem, at least ~1024 elements each, each a
+        // multiple of 4 elements long (but the last), so that every chunk starts
+        // on a 16-byte boundary (problems start on one: see total below)
         const int nc = (int)std::min<int64_t>(kMaxChunksPerProblem, std::max<int64_t>(1, (dim + 1023) / 1024));
-        const int64_t clen = (dim + nc - 1) / nc;
+        const int64_t clen = ((dim + nc - 1) / nc + 3) & ~int64_t(3);
         prob_chunk0.push_back((int)chunk_prob.size());
         int made = 0;
         for (int64_t s0 = 0; s0 < dim; s0 += clen, ++made) {
@@ -176,7 +178,7 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
         }
         prob_nchunk.push_back(made);
         prob_off.push_back(total);
-        total += dim;
+        total += (dim + 3) & ~int64_t(3);     // next problem on a 4-element boundary
         e_off += om;
         g_off += (int64_t)om * om;
         max_omega = std::max(max_omega, om);

@@ -45,6 +45,17 @@ extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(int n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int kMaxOmega = 62;
+
+// FP32 phase of the mixed form: stop giving cycles to FP32 vectors once the
+// restart residual rel no longer falls.  old is its value three cycles
+// earlier; FP32 stops when rel fell by less than 5 % over those cycles, or by
+// less than 30 % within 20x of the FP32 target (the rounding floor of FP32
+// vectors lies near that target).  A residual that falls slowly far above the
+// target is slow convergence, which FP32 cycles serve as well as FP64 ones.
+__host__ __device__ inline bool fp32_stalled(double rel, double old, double target)
+{
+    return rel > 0.95 * old || (rel < 20.0 * target && rel > 0.7 * old);
+}
 constexpr int kPackBytes = 16;       // streaming kernels move 16-byte packs of vector elements
 constexpr int kMaxLow = 13;          // L <= 13: rank table of 2^L uint16 in shared memory
 constexpr int kMaxWindow = 64;       // Lanczos vectors per cycle
@@ -359,7 +370,9 @@ struct BatchState {                  // one problem (device memory)
 struct BatchVec {                    // vectors concatenated over problems, cut into chunks
     int count;
     int nchunks;                     // every chunk lies inside one problem; <= 32 per problem
-    int64_t total;
+    int64_t total;                   // elements per vector: every problem starts on a 4-element
+                                     // boundary, and so does every chunk (up to 3 unused
+                                     // elements after each problem)
     const int *chunk_prob;
     const int64_t *chunk_start;      // global element index
     const int *chunk_len;

@@ -538,24 +538,39 @@ residual_kernel(const double *__restrict__ a, const double *__restrict__ b,
 }
 
 // ---- batched (segmented) kernels: vectors concatenated over problems ---------
+// Every chunk starts on a 16-byte boundary (problems and chunks are laid out on
+// 4-element boundaries, and so is the stride between window vectors), so the
+// kernels move 16-byte packs; the last pack of a chunk is read zero-filled and
+// written element by element.
+template <typename T>
+__host__ __device__ constexpr int seg_w() { return kPackBytes / (int)sizeof(T); }
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ v,
                 const BatchState *__restrict__ S, int use_skip, double *__restrict__ part)
 {
+    constexpr int W = seg_w<T>();
     __shared__ double sh[kThreads / 32];
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
         const int pr = V.chunk_prob[c];
         if (use_skip && S[pr].skip) continue;                // CTA-uniform
         const int64_t e0 = V.chunk_start[c];
         const int len = V.chunk_len[c];
+        const int np = (len + W - 1) / W;
         for (int j0 = 0; j0 < m; j0 += kGroup) {
             DotAcc<T> acc[kGroup];
-            for (int e = threadIdx.x; e < len; e += kThreads) {
-                const T pv = v[e0 + e];
+            for (int e = threadIdx.x; e < np; e += kThreads) {
+                const Pack<T, W> pv = load_pack<T, W, true>(v + e0, e, len);
+                Pack<T, W> q[kGroup];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u)
-                    if (j0 + u < m) acc[u].add(__ldg(Q + (int64_t)(j0 + u) * ldq + e0 + e), pv);
+                    if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq + e0, e, len);
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], pv.v[k]);
             }
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
@@ -589,6 +604,7 @@ __global__ void __launch_bounds__(kThreads)
 seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int i, T *__restrict__ v,
                          const BatchState *__restrict__ S, double *__restrict__ part)
 {
+    constexpr int W = seg_w<T>();
     __shared__ double sh[kThreads / 32];
     const int m = i + 1;
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
@@ -598,20 +614,30 @@ seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq,
         const T b = (T)(i > 0 ? S[pr].beta[i - 1] : 0.0);
         const int64_t e0 = V.chunk_start[c];
         const int len = V.chunk_len[c];
+        const int np = (len + W - 1) / W;
+        T *vc = v + e0;
         const T *qi = Q + (int64_t)i * ldq + e0;
         const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq + e0;
         for (int j0 = 0; j0 < m; j0 += kGroup) {
             DotAcc<T> acc[kGroup];
-            for (int e = threadIdx.x; e < len; e += kThreads) {
-                T x = v[e0 + e];
-                if (j0 == 0) {                                  // same thread, same element in later groups
-                    x = fma_t<T>(-a, __ldg(qi + e), x);
-                    if (i > 0) x = fma_t<T>(-b, __ldg(qm + e), x);
-                    v[e0 + e] = x;
+            for (int e = threadIdx.x; e < np; e += kThreads) {
+                Pack<T, W> x = load_pack<T, W, false>(vc, e, len);
+                if (j0 == 0) {                                  // same thread, same pack in later groups
+                    const Pack<T, W> yi = load_pack<T, W, true>(qi, e, len);
+                    const Pack<T, W> ym = load_pack<T, W, true>(qm, e, len);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) x.v[k] = fma_t<T>(-b, ym.v[k], fma_t<T>(-a, yi.v[k], x.v[k]));
+                    store_pack<T, W>(vc, e, len, x);
                 }
+                Pack<T, W> q[kGroup];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u)
-                    if (j0 + u < m) acc[u].add(__ldg(Q + (int64_t)(j0 + u) * ldq + e0 + e), x);
+                    if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq + e0, e, len);
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], x.v[k]);
             }
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
@@ -629,6 +655,7 @@ __global__ void __launch_bounds__(kThreads)
 seg_update_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, T *__restrict__ v,
                   const BatchState *__restrict__ S, double *__restrict__ part)
 {
+    constexpr int W = seg_w<T>();
     __shared__ T sc[kMaxWindow];
     __shared__ double sh[kThreads / 32];
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
@@ -639,12 +666,25 @@ seg_update_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m,
         __syncthreads();
         const int64_t e0 = V.chunk_start[c];
         const int len = V.chunk_len[c];
+        const int np = (len + W - 1) / W;
+        T *vc = v + e0;
         DotAcc<T> nrm;
-        for (int e = threadIdx.x; e < len; e += kThreads) {
-            T x = v[e0 + e];
-            for (int j = 0; j < m; ++j) x = fma_t<T>(-sc[j], __ldg(Q + (int64_t)j * ldq + e0 + e), x);
-            v[e0 + e] = x;
-            nrm.add(x, x);
+        for (int e = threadIdx.x; e < np; e += kThreads) {
+            Pack<T, W> x = load_pack<T, W, false>(vc, e, len);
+            for (int j0 = 0; j0 < m; j0 += kGroup) {
+                Pack<T, W> q[kGroup];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq + e0, e, len);
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) x.v[k] = fma_t<T>(-sc[j0 + u], q[u].v[k], x.v[k]);
+            }
+            store_pack<T, W>(vc, e, len, x);
+#pragma unroll
+            for (int k = 0; k < W; ++k) nrm.add(x.v[k], x.v[k]);
         }
         const double sum = block_reduce(nrm, sh);
         if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
@@ -653,9 +693,9 @@ seg_update_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m,
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-seg_scale_kernel(const BatchVec V, const T *__restrict__ src, T *__restrict__ dst, const BatchState *__restrict__ S,
-                 int i, int mode)
+seg_scale_kernel(const BatchVec V, const T *src, T *dst, const BatchState *__restrict__ S, int i, int mode)
 {
+    constexpr int W = seg_w<T>();
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
         const int pr = V.chunk_prob[c];
         if (mode == 0 ? S[pr].skip : S[pr].done) continue;
@@ -663,7 +703,13 @@ seg_scale_kernel(const BatchVec V, const T *__restrict__ src, T *__restrict__ ds
         const T f = (T)(d > 0.0 ? 1.0 / d : 0.0);
         const int64_t e0 = V.chunk_start[c];
         const int len = V.chunk_len[c];
-        for (int e = threadIdx.x; e < len; e += kThreads) dst[e0 + e] = src[e0 + e] * f;
+        const int np = (len + W - 1) / W;
+        for (int e = threadIdx.x; e < np; e += kThreads) {
+            Pack<T, W> x = load_pack<T, W, false>(src + e0, e, len);
+#pragma unroll
+            for (int k = 0; k < W; ++k) x.v[k] = x.v[k] * f;
+            store_pack<T, W>(dst + e0, e, len, x);
+        }
     }
 }
 
@@ -672,6 +718,7 @@ __global__ void __launch_bounds__(kThreads)
 seg_ritz_kernel(const BatchVec V, T *__restrict__ Q, int64_t ldq, const BatchState *__restrict__ S,
                 double *__restrict__ part)
 {
+    constexpr int W = seg_w<T>();
     __shared__ T ss[kMaxWindow];
     __shared__ double sh[kThreads / 32];
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
@@ -683,12 +730,26 @@ seg_ritz_kernel(const BatchVec V, T *__restrict__ Q, int64_t ldq, const BatchSta
         __syncthreads();
         const int64_t e0 = V.chunk_start[c];
         const int len = V.chunk_len[c];
+        const int np = (len + W - 1) / W;
         DotAcc<T> nrm;
-        for (int e = threadIdx.x; e < len; e += kThreads) {
-            T x = T(0);
-            for (int j = 0; j < m; ++j) x = fma_t<T>(ss[j], Q[(int64_t)j * ldq + e0 + e], x);
-            Q[e0 + e] = x;
-            nrm.add(x, x);
+        for (int e = threadIdx.x; e < np; e += kThreads) {
+            Pack<T, W> x;
+#pragma unroll
+            for (int k = 0; k < W; ++k) x.v[k] = T(0);
+            for (int j0 = 0; j0 < m; j0 += kGroup) {
+                Pack<T, W> q[kGroup];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) q[u] = load_pack<T, W, false>(Q + (int64_t)(j0 + u) * ldq + e0, e, len);
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) x.v[k] = fma_t<T>(ss[j0 + u], q[u].v[k], x.v[k]);
+            }
+            store_pack<T, W>(Q + e0, e, len, x);              // Q_0, in place: this thread read it above
+#pragma unroll
+            for (int k = 0; k < W; ++k) nrm.add(x.v[k], x.v[k]);
         }
         const double sum = block_reduce(nrm, sh);
         if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow] = sum;
@@ -770,7 +831,7 @@ __global__ void batch_converge_kernel(BatchState *S, int count, double tol, int 
     if (!stop && stall_check) {
         const double old = P.hist[0];
         P.hist[0] = P.hist[1]; P.hist[1] = P.hist[2]; P.hist[2] = P.hist[3]; P.hist[3] = rel;
-        if (cycle >= 3 && rel > 0.7 * old) { stop = true; P.stalled = 1; }
+        if (cycle >= 3 && fp32_stalled(rel, old, tol)) { stop = true; P.stalled = 1; }
     }
     if (stop) {
         P.done = 1;
