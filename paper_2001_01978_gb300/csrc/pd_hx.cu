@@ -423,6 +423,218 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Shared-memory view of variant 2 (one CTA's dynamic shared memory)
+template <typename T, typename A>
+struct Smem2 {
+    A *G, *GS, *GE, *d;
+    uint16_t *rank, *low;
+    uint64_t *bin, *occ, *emp;
+    T *x, *xn;
+    HHop<A> *hh;
+    __device__ Smem2(unsigned char *smem, const Layout2 &lay)
+        : G(reinterpret_cast<A *>(smem + lay.g)), GS(reinterpret_cast<A *>(smem + lay.gs)),
+          GE(reinterpret_cast<A *>(smem + lay.ge)), d(reinterpret_cast<A *>(smem + lay.d)),
+          rank(reinterpret_cast<uint16_t *>(smem + lay.rank)), low(reinterpret_cast<uint16_t *>(smem + lay.low)),
+          bin(reinterpret_cast<uint64_t *>(smem + lay.bin)), occ(reinterpret_cast<uint64_t *>(smem + lay.occ)),
+          emp(reinterpret_cast<uint64_t *>(smem + lay.emp)), x(reinterpret_cast<T *>(smem + lay.x)),
+          xn(reinterpret_cast<T *>(smem + lay.xn)), hh(reinterpret_cast<HHop<A> *>(smem + lay.hh))
+    {
+    }
+};
+
+// One problem's tables into shared memory, read for the whole launch (or, in
+// the batch, until the problem changes): G, d = 2e + diag(G), the rank and
+// low-word tables of L-bit words, and the binomials C(L + p, m) of the high
+// orbits (p < H, m <= N) that block_base_s adds up.
+template <typename T, typename A>
+__device__ __forceinline__ void load_tables2(const Smem2<T, A> &s, int omega, int L, int H, int N,
+                                             const A *__restrict__ G, const A *__restrict__ d,
+                                             const uint16_t *__restrict__ rankL, const uint16_t *__restrict__ lowword,
+                                             const uint64_t *__restrict__ binom)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < omega * omega; i += kThreads) s.G[i] = G[i];
+    for (int i = tid; i < omega; i += kThreads) s.d[i] = d[i];
+    for (int i = tid; i < (1 << L); i += kThreads) {
+        s.rank[i] = rankL[i];
+        s.low[i] = lowword[i];
+    }
+    for (int i = tid; i < (H > 0 ? H : 1) * (N + 1); i += kThreads) {
+        const int p = i / (N + 1), m = i - p * (N + 1);
+        s.bin[i] = __ldg(binom + (L + p) * kBinomStride + m);
+    }
+}
+
+// One basis block (high word h, first index base) of y = H x in variant 2.
+// x and y point at the problem's own vector; s holds its tables.  Called by
+// every thread of the CTA after a barrier that frees the previous block's
+// shared memory; it contains two barriers.  Any cp.async the caller issued
+// before is completed by the first of them.  swdot (nullable): x^T y per warp.
+template <typename T, typename A, int R>
+__device__ __forceinline__ void hx2_block(const Smem2<T, A> &s, const int omega, const int L, const int H,
+                                          const int N, const uint64_t h, const uint64_t base,
+                                          const T *__restrict__ x, T *__restrict__ y, double *swdot)
+{
+    const int tid = threadIdx.x;
+    const uint32_t maskL = (1u << L) - 1u;
+    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
+    const int ph = __popcll(h);
+    const int k = N - ph;
+    const int nemp = H - ph;
+    const int nhh = ph * nemp;
+    // block sizes C(L, k), C(L, k+1), C(L, k-1) from row p = 0 of s.bin
+    // (k + 1 <= N whenever a block h - o exists, i.e. ph > 0)
+    const int nk = (int)s.bin[k];
+    const int n_up = (k < L && ph > 0) ? (int)s.bin[k + 1] : 0;
+    const int n_dn = (k > 0 && nemp > 0) ? (int)s.bin[k - 1] : 0;
+    int lo_off = 0;                               // words of popcount k start here in s.low
+    for (int j = 0; j < k; ++j) lo_off += (int)s.bin[j];
+    const uint16_t *lw = s.low + lo_off;
+    T *sxn = s.xn;
+    T *sxd = sxn + ph * n_up;                     // staged blocks h + e start here
+
+    for (int r = tid; r < nk; r += kThreads) cp_async_elem(s.x + r, x + base + r);
+    cp_async_commit();
+
+    for (int t = tid; t < nhh; t += kThreads) {
+        const int a = t / nemp, c = t - a * nemp;
+        const int o = nth_set_bit(h, a);
+        const int q = nth_set_bit(~h & maskH, c);
+        s.hh[t].base = block_base_s(h ^ (1ull << o) ^ (1ull << q), N, s.bin);
+        s.hh[t].g = s.G[(L + q) * omega + (L + o)];
+    }
+    for (int t = tid; t < H; t += kThreads) {
+        const uint64_t bit = 1ull << t;
+        if (h & bit) {
+            const int j = __popcll(h & (bit - 1));
+            s.occ[j] = n_up ? block_base_s(h ^ bit, N, s.bin) : 0;
+            for (int e = 0; e < L; ++e) s.GS[j * L + e] = s.G[e * omega + L + t];
+        } else {
+            const int j = __popcll(~h & maskH & (bit - 1));
+            s.emp[j] = n_dn ? block_base_s(h | bit, N, s.bin) : 0;
+            for (int o = 0; o < L; ++o) s.GE[j * L + o] = s.G[(L + t) * omega + o];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();                              // own block, hop tables and slot bases visible
+
+    if (n_up)
+        for (int j = 0; j < ph; ++j) {
+            const T *src = x + s.occ[j];
+            T *dst = sxn + j * n_up;
+            for (int r = tid; r < n_up; r += kThreads) cp_async_elem(dst + r, src + r);
+        }
+    if (n_dn)
+        for (int j = 0; j < nemp; ++j) {
+            const T *src = x + s.emp[j];
+            T *dst = sxd + j * n_dn;
+            for (int r = tid; r < n_dn; r += kThreads) cp_async_elem(dst + r, src + r);
+        }
+    cp_async_commit();
+
+    A Dh = A(0);
+    for (uint64_t w = h; w; w &= w - 1) Dh += s.d[L + __ffsll((long long)w) - 1];
+
+    uint32_t lr[R];
+    A acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        lr[i] = 0;
+        acc[i] = A(0);
+        if (r < nk) {
+            const uint32_t l = lw[r];
+            lr[i] = l;
+            A D = A(0);
+            for (uint32_t w = l; w; w &= w - 1) D += s.d[__ffs(w) - 1];
+            acc[i] = (D + Dh) * A(s.x[r]);
+        }
+    }
+
+    // low -> low
+    if (k > 0 && k < L) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (tid + i * kThreads < nk) {
+                const uint32_t l = lr[i];
+                A a = acc[i];
+                uint32_t occ = l;
+                for (int u = 0; u < k; ++u) {
+                    const int o = __ffs(occ) - 1;
+                    occ &= occ - 1;
+                    const uint32_t lo = l ^ (1u << o);
+                    const A *gcol = s.G + o;
+                    uint32_t emp = ~l & maskL;
+                    for (int v = 0; v < L - k; ++v) {
+                        const int q = __ffs(emp) - 1;
+                        emp &= emp - 1;
+                        a += gcol[q * omega] * A(s.x[s.rank[lo | (1u << q)]]);
+                    }
+                }
+                acc[i] = a;
+            }
+        }
+    }
+
+    // high -> high: same offsets in the target block
+    for (int j = 0; j < nhh; ++j) {
+        const T *xb = x + s.hh[j].base;
+        const A g = s.hh[j].g;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) acc[i] += g * A(__ldg(xb + r));
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();                              // staged neighbour blocks visible
+
+    // high -> low: pair from occupied high orbit L+t to empty low orbit e;
+    // the target offset rank(l + e) is the same in every staged block
+    if (n_up) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) {
+                const uint32_t l = lr[i];
+                A a = acc[i];
+                for (uint32_t w = ~l & maskL; w; w &= w - 1) {
+                    const int e = __ffs(w) - 1;
+                    const A *g = s.GS + e;
+                    const T *xp = sxn + s.rank[l | (1u << e)];
+                    for (int j = 0; j < ph; ++j) a += g[j * L] * A(xp[j * n_up]);
+                }
+                acc[i] = a;
+            }
+        }
+    }
+    // low -> high: pair from occupied low orbit o to empty high orbit L+t
+    if (n_dn) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * kThreads;
+            if (r < nk) {
+                const uint32_t l = lr[i];
+                A a = acc[i];
+                for (uint32_t w = l; w; w &= w - 1) {
+                    const int o = __ffs(w) - 1;
+                    const A *g = s.GE + o;
+                    const T *xp = sxd + s.rank[l ^ (1u << o)];
+                    for (int j = 0; j < nemp; ++j) a += g[j * L] * A(xp[j * n_dn]);
+                }
+                acc[i] = a;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        if (r < nk) y[base + r] = T(acc[i]);
+    }
+    if (swdot) warp_dot<T, A, R>(acc, s.x, nk, swdot);
+}
+
 // Same product as hx_kernel.  Differences: all ph blocks h - o (k+1 low pairs)
 // and all H-ph blocks h + e (k-1) are staged together; the coefficients of the
 // high<->low hops are laid out per staged block (G_{e, L+t} for block h - t at
@@ -451,39 +663,15 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     __shared__ double sred[kThreads / 32];
     __shared__ double swdot[kThreads / 32];
     const int omega = B.omega, L = B.L, H = B.H, N = B.n;
-    const Layout2 lay = layout2<T, A>(omega, L, H, N, B.max_block, B.max_hh, B.max_stage);
-    A *sG = reinterpret_cast<A *>(smem + lay.g);
-    A *sGS = reinterpret_cast<A *>(smem + lay.gs);
-    A *sGE = reinterpret_cast<A *>(smem + lay.ge);
-    A *sd = reinterpret_cast<A *>(smem + lay.d);
-    uint16_t *sRank = reinterpret_cast<uint16_t *>(smem + lay.rank);
-    uint16_t *sLow = reinterpret_cast<uint16_t *>(smem + lay.low);
-    uint64_t *sBin = reinterpret_cast<uint64_t *>(smem + lay.bin);
-    T *sx = reinterpret_cast<T *>(smem + lay.x);
-    T *sxn = reinterpret_cast<T *>(smem + lay.xn);
-    HHop<A> *sHH = reinterpret_cast<HHop<A> *>(smem + lay.hh);
-    uint64_t *sOccB = reinterpret_cast<uint64_t *>(smem + lay.occ);
-    uint64_t *sEmpB = reinterpret_cast<uint64_t *>(smem + lay.emp);
+    const Smem2<T, A> s(smem, layout2<T, A>(omega, L, H, N, B.max_block, B.max_hh, B.max_stage));
     const int tid = threadIdx.x;
-
-    for (int i = tid; i < omega * omega; i += kThreads) sG[i] = Gg[i];
-    for (int i = tid; i < omega; i += kThreads) sd[i] = dg[i];
-    for (int i = tid; i < (1 << L); i += kThreads) {
-        sRank[i] = B.rankL[i];
-        sLow[i] = B.lowword[i];
-    }
-    for (int i = tid; i < (H > 0 ? H : 1) * (N + 1); i += kThreads) {
-        const int p = i / (N + 1), m = i - p * (N + 1);
-        sBin[i] = __ldg(B.binom + (L + p) * kBinomStride + m);
-    }
-    const uint32_t maskL = (1u << L) - 1u;
-    const uint64_t maskH = (H >= 64) ? ~0ull : ((1ull << H) - 1ull);
+    load_tables2<T, A>(s, omega, L, H, N, Gg, dg, B.rankL, B.lowword, B.binom);
 
     // block schedule: slot it holds (index, h, base) of the block of iteration
     // it.  Thread 0 holds the index of the next block in nb1; during the
     // current block it copies that block's (h, base) into slot it ^ 1 with
-    // cp.async (completed by its cp.async waits below) and takes the index
-    // after it from the counter, so neither latency delays a block.
+    // cp.async (completed by the first barrier of hx2_block) and takes the
+    // index after it from the counter, so neither latency delays a block.
     // (Block counts are below 2^31: build_tables rejects more blocks.)
     const int nblocks = (int)B.nblocks;
     int nb1 = 0;
@@ -510,161 +698,7 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
             }
         }
         if (b >= nblocks) break;
-
-        const uint64_t h = s_h[it];
-        const uint64_t base = s_base[it];
-        const int ph = __popcll(h);
-        const int k = N - ph;
-        const int nemp = H - ph;
-        const int nhh = ph * nemp;
-        // block sizes C(L, k), C(L, k+1), C(L, k-1) from row p = 0 of sBin
-        // (k + 1 <= N whenever a block h - o exists, i.e. ph > 0)
-        const int nk = (int)sBin[k];
-        const int n_up = (k < L && ph > 0) ? (int)sBin[k + 1] : 0;
-        const int n_dn = (k > 0 && nemp > 0) ? (int)sBin[k - 1] : 0;
-        const uint16_t *lw = sLow + B.lo_off[k];
-        T *sxd = sxn + ph * n_up;                 // staged blocks h + e start here
-
-        for (int r = tid; r < nk; r += kThreads) cp_async_elem(sx + r, x + base + r);
-        cp_async_commit();
-
-        for (int t = tid; t < nhh; t += kThreads) {
-            const int a = t / nemp, c = t - a * nemp;
-            const int o = nth_set_bit(h, a);
-            const int q = nth_set_bit(~h & maskH, c);
-            sHH[t].base = block_base_s(h ^ (1ull << o) ^ (1ull << q), N, sBin);
-            sHH[t].g = sG[(L + q) * omega + (L + o)];
-        }
-        for (int t = tid; t < H; t += kThreads) {
-            const uint64_t bit = 1ull << t;
-            if (h & bit) {
-                const int j = __popcll(h & (bit - 1));
-                sOccB[j] = n_up ? block_base_s(h ^ bit, N, sBin) : 0;
-                for (int e = 0; e < L; ++e) sGS[j * L + e] = sG[e * omega + L + t];
-            } else {
-                const int j = __popcll(~h & maskH & (bit - 1));
-                sEmpB[j] = n_dn ? block_base_s(h | bit, N, sBin) : 0;
-                for (int o = 0; o < L; ++o) sGE[j * L + o] = sG[(L + t) * omega + o];
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();                          // own block, hop tables and slot bases visible
-
-        if (n_up)
-            for (int j = 0; j < ph; ++j) {
-                const T *src = x + sOccB[j];
-                T *dst = sxn + j * n_up;
-                for (int r = tid; r < n_up; r += kThreads) cp_async_elem(dst + r, src + r);
-            }
-        if (n_dn)
-            for (int j = 0; j < nemp; ++j) {
-                const T *src = x + sEmpB[j];
-                T *dst = sxd + j * n_dn;
-                for (int r = tid; r < n_dn; r += kThreads) cp_async_elem(dst + r, src + r);
-            }
-        cp_async_commit();
-
-        A Dh = A(0);
-        for (uint64_t w = h; w; w &= w - 1) Dh += sd[L + __ffsll((long long)w) - 1];
-
-        uint32_t lr[R];
-        A acc[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int r = tid + i * kThreads;
-            lr[i] = 0;
-            acc[i] = A(0);
-            if (r < nk) {
-                const uint32_t l = lw[r];
-                lr[i] = l;
-                A D = A(0);
-                for (uint32_t w = l; w; w &= w - 1) D += sd[__ffs(w) - 1];
-                acc[i] = (D + Dh) * A(sx[r]);
-            }
-        }
-
-        // low -> low
-        if (k > 0 && k < L) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                if (tid + i * kThreads < nk) {
-                    const uint32_t l = lr[i];
-                    A a = acc[i];
-                    uint32_t occ = l;
-                    for (int u = 0; u < k; ++u) {
-                        const int o = __ffs(occ) - 1;
-                        occ &= occ - 1;
-                        const uint32_t lo = l ^ (1u << o);
-                        const A *gcol = sG + o;
-                        uint32_t emp = ~l & maskL;
-                        for (int v = 0; v < L - k; ++v) {
-                            const int q = __ffs(emp) - 1;
-                            emp &= emp - 1;
-                            a += gcol[q * omega] * A(sx[sRank[lo | (1u << q)]]);
-                        }
-                    }
-                    acc[i] = a;
-                }
-            }
-        }
-
-        // high -> high: same offsets in the target block
-        for (int j = 0; j < nhh; ++j) {
-            const T *xb = x + sHH[j].base;
-            const A g = sHH[j].g;
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = tid + i * kThreads;
-                if (r < nk) acc[i] += g * A(__ldg(xb + r));
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();                          // staged neighbour blocks visible
-
-        // high -> low: pair from occupied high orbit L+t to empty low orbit e;
-        // the target offset rank(l + e) is the same in every staged block
-        if (n_up) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = tid + i * kThreads;
-                if (r < nk) {
-                    const uint32_t l = lr[i];
-                    A a = acc[i];
-                    for (uint32_t w = ~l & maskL; w; w &= w - 1) {
-                        const int e = __ffs(w) - 1;
-                        const A *g = sGS + e;
-                        const T *xp = sxn + sRank[l | (1u << e)];
-                        for (int j = 0; j < ph; ++j) a += g[j * L] * A(xp[j * n_up]);
-                    }
-                    acc[i] = a;
-                }
-            }
-        }
-        // low -> high: pair from occupied low orbit o to empty high orbit L+t
-        if (n_dn) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = tid + i * kThreads;
-                if (r < nk) {
-                    const uint32_t l = lr[i];
-                    A a = acc[i];
-                    for (uint32_t w = l; w; w &= w - 1) {
-                        const int o = __ffs(w) - 1;
-                        const A *g = sGE + o;
-                        const T *xp = sxd + sRank[l ^ (1u << o)];
-                        for (int j = 0; j < nemp; ++j) a += g[j * L] * A(xp[j * n_dn]);
-                    }
-                    acc[i] = a;
-                }
-            }
-        }
-
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int r = tid + i * kThreads;
-            if (r < nk) y[base + r] = T(acc[i]);
-        }
-        if (blk_part) warp_dot<T, A, R>(acc, sx, nk, swdot);
+        hx2_block<T, A, R>(s, omega, L, H, N, s_h[it], s_base[it], x, y, blk_part ? swdot : nullptr);
         prev = b;
         if (tid == 0) {                           // publish the next block (read after the barrier)
             s_idx[it ^ 1] = nb1;
