@@ -83,6 +83,34 @@ __device__ __forceinline__ void store_pack(T *a, int64_t c, int64_t n, const Pac
         if (e + k < n) a[e + k] = r.v[k];
 }
 
+// The CTA-wide sums of a group of accumulators in one pass: every warp reduces
+// each accumulator with shuffles and lane 0 keeps the warp's sums in shared
+// memory; after one barrier thread u adds accumulator u's warp sums in warp
+// order (a fixed order) and writes out[u].  nvalid (CTA-uniform) accumulators
+// are used; shg holds kGroup * kThreads / 32 doubles.  Ends with a barrier, so
+// shg can be reused at once.
+template <typename T>
+__device__ __forceinline__ void block_reduce_group(const DotAcc<T> (&acc)[kGroup], int nvalid, double *shg,
+                                                   double *out)
+{
+    constexpr int NW = kThreads / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+        if (u < nvalid) {
+            const double v = warp_reduce(acc[u]);
+            if (lane == 0) shg[u * NW + w] = v;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nvalid) {
+        double sum = 0.0;
+        for (int i = 0; i < NW; ++i) sum += shg[threadIdx.x * NW + i];
+        out[threadIdx.x] = sum;
+    }
+    __syncthreads();
+}
+
 // Lanczos step bookkeeping (Algorithm 2): alpha_i = alpha + c_i (the second
 // Gram-Schmidt pass corrects the recurrence's alpha), beta_i = ||p||; a beta_i
 // below 1e-13 of the running matrix-norm estimate ends the cycle (an invariant
@@ -109,7 +137,7 @@ dots_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p
             const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];
+    __shared__ double shg[kGroup * (kThreads / 32)];
     const int64_t nc = (n + W - 1) / W;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t c0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -127,13 +155,7 @@ dots_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p
 #pragma unroll
                     for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], pv.v[k]);
         }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            if (j0 + u < m) {
-                const double s = block_reduce(acc[u], sh);
-                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
-            }
-        }
+        block_reduce_group<T>(acc, min(kGroup, m - j0), shg, part + (int64_t)blockIdx.x * kMaxWindow + j0);
     }
     if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, m, out);
 }
@@ -150,7 +172,7 @@ recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosS
                      unsigned long long *ticket, const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    __shared__ double sh[kThreads / 32];
+    __shared__ double shg[kGroup * (kThreads / 32)];
     const int m = i + 1;
     const T a = (T)S->c1[0];
     const T b = (T)(i > 0 ? S->beta[i - 1] : 0.0);
@@ -194,13 +216,7 @@ recur_project_kernel(const T *__restrict__ Q, int64_t ldq, int i, const LanczosS
 #pragma unroll
                     for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], v.v[k]);
         }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            if (j0 + u < m) {
-                const double s = block_reduce(acc[u], sh);
-                if (threadIdx.x == 0) part[blockIdx.x * kMaxWindow + j0 + u] = s;
-            }
-        }
+        block_reduce_group<T>(acc, min(kGroup, m - j0), shg, part + (int64_t)blockIdx.x * kMaxWindow + j0);
     }
     if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, m, out);
 }
@@ -551,7 +567,7 @@ seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, c
                 const BatchState *__restrict__ S, int use_skip, double *__restrict__ part)
 {
     constexpr int W = seg_w<T>();
-    __shared__ double sh[kThreads / 32];
+    __shared__ double shg[kGroup * (kThreads / 32)];
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
         const int pr = V.chunk_prob[c];
         if (use_skip && S[pr].skip) continue;                // CTA-uniform
@@ -572,13 +588,7 @@ seg_dots_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq, int m, c
 #pragma unroll
                         for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], pv.v[k]);
             }
-#pragma unroll
-            for (int u = 0; u < kGroup; ++u) {
-                if (j0 + u < m) {
-                    const double sum = block_reduce(acc[u], sh);
-                    if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
-                }
-            }
+            block_reduce_group<T>(acc, min(kGroup, m - j0), shg, part + (int64_t)c * kMaxWindow + j0);
         }
     }
 }
@@ -605,7 +615,7 @@ seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq,
                          const BatchState *__restrict__ S, double *__restrict__ part)
 {
     constexpr int W = seg_w<T>();
-    __shared__ double sh[kThreads / 32];
+    __shared__ double shg[kGroup * (kThreads / 32)];
     const int m = i + 1;
     for (int c = blockIdx.x; c < V.nchunks; c += gridDim.x) {
         const int pr = V.chunk_prob[c];
@@ -639,13 +649,7 @@ seg_recur_project_kernel(const BatchVec V, const T *__restrict__ Q, int64_t ldq,
 #pragma unroll
                         for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], x.v[k]);
             }
-#pragma unroll
-            for (int u = 0; u < kGroup; ++u) {
-                if (j0 + u < m) {
-                    const double sum = block_reduce(acc[u], sh);
-                    if (threadIdx.x == 0) part[(int64_t)c * kMaxWindow + j0 + u] = sum;
-                }
-            }
+            block_reduce_group<T>(acc, min(kGroup, m - j0), shg, part + (int64_t)c * kMaxWindow + j0);
         }
     }
 }
