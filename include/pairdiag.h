@@ -295,6 +295,21 @@ int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, 
 int pairdiag_tune_set(int omega, int n_pairs, int precision, int low_bits, int hx_variant);
 int pairdiag_tune_get(int omega, int n_pairs, int precision, int *low_bits, int *hx_variant);
 
+/* ------------------------------------------------------ device memory ---- */
+
+/*
+ * The library keeps the device blocks of destroyed handles (and of finished
+ * batch calls) in a process-wide cache, per device and rounded size, and hands
+ * them to the next handle that needs the same sizes: a loop of create / solve /
+ * destroy then allocates once.  The paper has no counterpart (its Fortran
+ * allocates host arrays).  When cudaMalloc runs out of memory the cache is
+ * emptied once and the allocation retried.
+ * pairdiag_release_cache returns every cached block to the driver (cudaFree);
+ * released_bytes (nullable, host) receives their total size.  Blocks still
+ * owned by live handles are not touched.  Thread-safe; always PD_OK.
+ */
+int pairdiag_release_cache(size_t *released_bytes);
+
 /* ------------------------------------------------------- diagnostics ---- */
 
 /* Number of CUDA kernels this library has launched since it was loaded (all

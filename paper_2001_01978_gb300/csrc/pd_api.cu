@@ -156,15 +156,17 @@ void free_all(pairdiag *h)
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    // the blocks go back to the library's cache: no queued kernel may still use
+    // them (cudaFree gave the same guarantee by synchronising the device)
+    cudaDeviceSynchronize();
+    for (void *p : ptrs) pool_free(p);
 }
 
 template <typename T>
 int dalloc(T **p, size_t count)
 {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    cudaError_t e = pool_alloc(&q, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA, "cudaMalloc(%zu bytes): %s",
@@ -255,9 +257,13 @@ int ensure_window(pairdiag *h, int dtype, int window)
 {
     const size_t es = dtype == 0 ? sizeof(double) : sizeof(float);
     if (h->d_Q[dtype] && h->Qwin[dtype] >= window) return PD_OK;
-    if (h->d_Q[dtype]) { cudaFree(h->d_Q[dtype]); h->d_Q[dtype] = nullptr; }
+    if (h->d_Q[dtype]) {                          // a larger window: the old one may still be in use
+        cudaStreamSynchronize(h->st);
+        pool_free(h->d_Q[dtype]);
+        h->d_Q[dtype] = nullptr;
+    }
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, es * (size_t)window * (size_t)h->ldq);
+    cudaError_t e = pool_alloc(&q, es * (size_t)window * (size_t)h->ldq);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(PD_ENOMEM, "Lanczos window of %d x %lld elements: %s", window, (long long)h->dim,
@@ -266,7 +272,7 @@ int ensure_window(pairdiag *h, int dtype, int window)
     h->d_Q[dtype] = q;
     h->Qwin[dtype] = window;
     if (!h->d_p[dtype]) {
-        e = cudaMalloc(&h->d_p[dtype], es * (size_t)h->dim);
+        e = pool_alloc(&h->d_p[dtype], es * (size_t)h->dim);
         if (e != cudaSuccess) { cudaGetLastError(); return fail(PD_ENOMEM, "work vector: %s", cudaGetErrorString(e)); }
     }
     return PD_OK;
@@ -740,7 +746,8 @@ int pairdiag_basis(const pairdiag_t *h, uint64_t *out)
         cudaError_t e2 = cudaStreamSynchronize(h->st);
         if (e1 != cudaSuccess || e2 != cudaSuccess) st = fail(PD_ECUDA, "basis copy failed");
     }
-    cudaFree(d);
+    cudaStreamSynchronize(h->st);
+    pool_free(d);
     return st;
 }
 

@@ -32,13 +32,14 @@ struct DevBuf {
     std::vector<void *> ptrs;
     ~DevBuf()
     {
-        for (void *p : ptrs) cudaFree(p);
+        cudaDeviceSynchronize();                // as cudaFree did: nothing queued still uses them
+        for (void *p : ptrs) pool_free(p);
     }
     template <typename T>
     int alloc(T **p, size_t count)
     {
         void *q = nullptr;
-        const cudaError_t e = cudaMalloc(&q, std::max<size_t>(16, count * sizeof(T)));
+        const cudaError_t e = pool_alloc(&q, std::max<size_t>(16, count * sizeof(T)));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(PD_ENOMEM, "batch: cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
@@ -255,7 +256,7 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
         const int hx_grid_ = hx_batch_grid(BB, dt);
         auto step = [&](int i) -> int {
             PD_CUDA(hx_batch_launch(BB, P, dt, q(i), pv, d_counter, hx_grid_, st, skip, skip_stride));
-            PD_CUDA(seg_dots_launch(dt, V, q(i), total, 1, pv, skip, part, &S[0].c1, sd, st));
+            PD_CUDA(seg_dots_launch(dt, V, q(i), total, 1, pv, S, part, &S[0].c1, sd, st));
             PD_CUDA(seg_recur_project_launch(dt, V, Q, total, i, pv, S, part, st));
             PD_CUDA(seg_update_launch(dt, V, Q, total, i + 1, pv, S, part, st));
             PD_CUDA(batch_finalize_launch(S, count, i, st));
@@ -273,7 +274,7 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
             return PD_OK;
         };
         // normalise the start vectors of the open problems
-        PD_CUDA(seg_dots_launch(dt, V, q(0), total, 1, q(0), skip, part, &S[0].norm2, sd, st));
+        PD_CUDA(seg_dots_launch(dt, V, q(0), total, 1, q(0), S, part, &S[0].norm2, sd, st));
         PD_CUDA(seg_scale_launch(dt, V, q(0), q(0), S, 0, 1, st));
 
         // capture the cycle tail once (replayed launches are added to the counter)

@@ -46,6 +46,15 @@ inline void count_launches(int n) { g_kernel_launches.fetch_add(n, std::memory_o
 
 constexpr int kMaxOmega = 62;
 
+// ---- device memory cache (pd_pool.cu) --------------------------------------
+// pool_alloc: a cached block of the same rounded size, else cudaMalloc (the
+// cache is emptied once and the call retried when the device is full).
+// pool_free: the block returns to the cache; no queued work may still use it.
+// Blocks not from the pool are passed to cudaFree.
+cudaError_t pool_alloc(void **p, size_t bytes);
+void pool_free(void *p);
+size_t pool_cached_bytes();
+
 // FP32 phase of the mixed form: stop giving cycles to FP32 vectors once the
 // restart residual rel no longer falls.  old is its value three cycles
 // earlier; FP32 stops when rel fell by less than 5 % over those cycles, or by
@@ -384,8 +393,9 @@ constexpr int kMaxChunksPerProblem = 32;
 
 // out[p * out_stride + j] = sum over problem p's elements of Q_j[e] v[e], j < m
 // (Q vector-major with leading dimension ldq); skipped problems are left alone
+// S (nullable): the problems' states; when given, problems with skip set are passed over
 cudaError_t seg_dots_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, const void *v,
-                            const int *skip, double *partials, double *out, int out_stride, cudaStream_t st);
+                            const BatchState *S, double *partials, double *out, int out_stride, cudaStream_t st);
 // per problem: v <- v - c1 q_i - beta[i-1] q_{i-1}; then c2[j] = Q_j^T v, j <= i
 cudaError_t seg_recur_project_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int i, void *v,
                                      BatchState *S, double *partials, cudaStream_t st);

@@ -1120,11 +1120,9 @@ cudaError_t residual_launch(const double *a, const double *b, const double *lamb
 
 // ---- batched launchers ---------------------------------------------------------
 cudaError_t seg_dots_launch(int dtype, const BatchVec &V, const void *Q, int64_t ldq, int m, const void *v,
-                            const int *skip, double *partials, double *out, int out_stride, cudaStream_t st)
+                            const BatchState *S, double *partials, double *out, int out_stride, cudaStream_t st)
 {
-    // skip != nullptr means: honour BatchState::skip (skip points at the state array)
-    const BatchState *S = reinterpret_cast<const BatchState *>(skip);
-    const int use_skip = skip != nullptr;
+    const int use_skip = S != nullptr;            // honour BatchState::skip
     const int g = seg_grid(V);
     if (dtype == 0)
         seg_dots_kernel<double><<<g, kThreads, 0, st>>>(V, (const double *)Q, ldq, m, (const double *)v, S, use_skip, partials);

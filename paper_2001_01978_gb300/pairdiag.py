@@ -77,6 +77,7 @@ _SIGNATURES = {
     "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
+    "pairdiag_release_cache": (ctypes.c_int, [_P]),
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
@@ -230,10 +231,17 @@ def pairdiag_set_start(h, v) -> None:
     _check(lib().pairdiag_set_start(h, _np_ptr(v)))
 
 
-def pairdiag_ground_state(h, tol: float, want_vector: bool = True) -> dict:
+def pairdiag_ground_state(h, tol: float, want_vector: bool = True, out: np.ndarray | None = None) -> dict:
+    """out (optional): a float64 host array of dim elements that receives the
+    eigenvector (pinned memory makes the copy faster); by default one is made."""
     e0 = ctypes.c_double()
     info = pairdiag_info()
-    vec = np.empty(pairdiag_dim(h), dtype=np.float64) if want_vector else None
+    if want_vector and out is not None:
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != pairdiag_dim(h):
+            raise ValueError("out must be a contiguous float64 array of dim elements")
+        vec = out
+    else:
+        vec = np.empty(pairdiag_dim(h), dtype=np.float64) if want_vector else None
     st = _check(lib().pairdiag_ground_state(h, tol, ctypes.byref(e0), _np_ptr(vec) if want_vector else None,
                                             ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
     return dict(e0=e0.value, vec=vec, status=st, **info.as_dict())
@@ -312,6 +320,13 @@ def pairdiag_tridiag_lowest(h, alpha, beta):
 
 def pairdiag_kernel_launches() -> int:
     return int(lib().pairdiag_kernel_launches())
+
+
+def pairdiag_release_cache() -> int:
+    """Return the library's cached device blocks to the driver; their bytes."""
+    n = ctypes.c_size_t()
+    _check(lib().pairdiag_release_cache(ctypes.byref(n)))
+    return n.value
 
 
 def pairdiag_set_profiling(h, on: bool) -> None:
@@ -448,8 +463,8 @@ class Solver:
     def nnz(self) -> int:
         return pairdiag_nnz(self.h)
 
-    def ground_state(self, tol: float, want_vector: bool = True) -> dict:
-        return pairdiag_ground_state(self.h, tol, want_vector)
+    def ground_state(self, tol: float, want_vector: bool = True, out: np.ndarray | None = None) -> dict:
+        return pairdiag_ground_state(self.h, tol, want_vector, out)
 
     def close(self):
         if self.h is not None:

@@ -225,3 +225,24 @@ def test_table3_large_rows_mixed(row):
     assert abs(r["e0"] - float(row[3])) <= 0.5e-7 + 1e-9
     ref = richardson.ground_energy(e, float(np.float32(-0.4)), n)
     assert abs(r["e0"] - ref) <= 1e-10 * abs(ref)
+
+
+def test_device_cache_reuse_and_release():
+    """Destroyed handles leave their device blocks in the library's cache; the
+    next handle of the same sizes reuses them and computes the same E0 (every
+    reduction has a fixed order, so bit for bit); releasing empties the cache."""
+    omega, n, e, G = pd_inputs.workload("omega24_n12_sepnoise_s1")
+    opt = dict(precision=pd.PD_PREC_MIXED, window=20, start=pd.PD_START_RANDOM, seed=3)
+    r1 = solve(omega, n, e, G, tol=1e-5, **opt)
+    r2 = solve(omega, n, e, G, tol=1e-5, **opt)
+    assert r1["status"] == r2["status"] == pd.PD_OK
+    assert r1["e0"] == r2["e0"] and r1["iterations"] == r2["iterations"]
+    assert pd.pairdiag_release_cache() > 0
+    assert pd.pairdiag_release_cache() == 0
+    r3 = solve(omega, n, e, G, tol=1e-5, **opt)
+    assert r3["e0"] == r1["e0"]
+    out = np.full(math.comb(omega, n), np.nan)
+    with pd.Solver(omega, n, e, G, **opt) as s:
+        r4 = s.ground_state(1e-5, out=out)
+    assert r4["vec"] is out and r4["e0"] == r1["e0"]
+    assert np.all(np.isfinite(out)) and abs(np.linalg.norm(out) - 1.0) < 1e-10
