@@ -252,8 +252,8 @@ typedef struct {
  *                    each exactly symmetric
  *   tol            : |beta_1/alpha_1| (Sec. 5.1); the mixed form refines every
  *                    vector in FP64 and reports that residual instead; problems
- *                    whose refined residual misses tol continue in FP64 cycles of
- *                    at most 8 Lanczos vectors from the refined vector
+ *                    whose refined residual misses tol continue in FP64 cycles from
+ *                    the refined vector
  *   opt            : nullable; window, max_restarts, precision, seed, low_bits and
  *                    mixed_floor are used; start PD_START_RANDOM or PD_START_MLP, mode 0
  *   mlp            : the warm-start network for PD_START_MLP (else nullable); one

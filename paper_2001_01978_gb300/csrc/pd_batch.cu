@@ -24,10 +24,6 @@ using namespace pd;
 
 namespace {
 
-// Lanczos window of the FP64 cycles that continue the mixed form's problems
-// whose refined residual missed tol
-constexpr int kContinuationWindow = 8;
-
 struct DevBuf {
     std::vector<void *> ptrs;
     ~DevBuf()
@@ -230,7 +226,7 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
     V.prob_chunk0 = d_pc0; V.prob_nchunk = d_pnc; V.prob_off = d_po;
     HxProblem P{d_G64, d_d64, d_G32, d_d32};
 
-    int m = std::min(opt.window, kMaxWindow);       // Lanczos window of the running phase
+    const int m = std::min(opt.window, kMaxWindow);
     double *part; BatchState *S; int *d_active, *d_counter;
     PD_TRY(buf.alloc(&part, (size_t)V.nchunks * kMaxWindow));
     PD_TRY(buf.alloc(&S, (size_t)count));
@@ -354,10 +350,6 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
             PD_CUDA(cudaMemcpyAsync(&reopened, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
             PD_CUDA(cudaStreamSynchronize(st));
             if (reopened > 0) {
-                // the continuation starts from the refined, nearly converged
-                // vector: short cycles serve it (measured on the 4096-problem
-                // workload: 5.40 s against 5.92 s with the full window)
-                m = std::min(m, kContinuationWindow);
                 PD_TRY(buf.alloc(&Q64, 8 * (size_t)m * (size_t)total));
                 PD_TRY(buf.alloc(&p64, 8 * (size_t)total));
                 PD_CUDA(cudaMemcpyAsync(Q64, v64, 8 * (size_t)total, cudaMemcpyDeviceToDevice, st));
