@@ -74,3 +74,20 @@ def test_workload_4096_stratified_subset():
                 ref = s.ground_state(1e-11, want_vector=False)["e0"]
         assert abs(r["e0"][i] - ref) <= 1e-8 * max(1.0, abs(ref)), (i, om, n, dims[i])
     assert np.mean(r["converged"]) >= 0.99
+
+
+def test_batch_on_reused_device_blocks():
+    """A batch call that receives the device blocks an earlier call left in the
+    library's cache (old data in them) gives the oracle's energies, and every
+    problem smaller than the window finishes within dim + 2 Lanczos steps, as
+    a Krylov space that spans it must (a skipped alpha dot stalls them)."""
+    probs = small_batch()
+    pd.pairdiag_batch_ground_state(probs, 1e-11, pd.pairdiag_default_options(precision=0, window=20))
+    r = pd.pairdiag_batch_ground_state(probs, 1e-6, pd.pairdiag_default_options(precision=1, window=20))
+    assert r["call_status"] == pd.PD_OK
+    for i, (om, n, e, G) in enumerate(probs):
+        ref = oracle.lanczos_ground(om, n, e, G, window=40, tol=1e-13)["e0"]
+        assert abs(r["e0"][i] - ref) <= 1e-8 * max(1.0, abs(ref)), (i, r["e0"][i], ref)
+        dim = math.comb(om, n)
+        if dim < 20:
+            assert r["iterations"][i] <= dim + 2, (i, dim, r["iterations"][i])
