@@ -371,7 +371,10 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (FP32 H*x) ----
     peak, peak_kind = measured_peaks()
     alg_bytes = nnz * 4 + 2 * dim * 4
-    avg_hx_s = (hx_ms / hx_count) * 1e-3
+    # per executed FP32 product: launches skipped after a cycle ended early (a
+    # converged Ritz pair) add their few microseconds to hx_ms, not to the count
+    hx_executed = sum(r["iterations_fp32"] for r in results)
+    avg_hx_s = (hx_ms / max(1, hx_executed)) * 1e-3
     achieved = alg_bytes / avg_hx_s / 1e9
     lb, hv = pd.pairdiag_tune_get(omega, n, pd.PD_PREC_MIXED)
     if args.low_bits:
@@ -380,7 +383,8 @@ def run_ours(args):
     roofline = {"kernel": "H*x FP32 (low_bits %d, variant %d)" % (lb or 12, hv or 1), "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_hx_s * 1e3,
-                "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": hx_ms / total_ms}
+                "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": hx_ms / total_ms,
+                "timed_launches": hx_count, "executed_products": hx_executed}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -538,7 +542,7 @@ def run_forms(args, workload, tag):
                 pd.pairdiag_ground_state_dev(s.h, args.tol, None)
             pd.pairdiag_set_profiling(s.h, True)
             pd.pairdiag_get_profile(s.h)                  # clear
-            times, r = [], None
+            times, r, executed = [], None, 0
             for i in range(max(1, args.steps)):
                 flush.fill_(1.0)
                 ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -547,17 +551,19 @@ def run_forms(args, workload, tag):
                 ev1.record(stream)
                 ev1.synchronize()
                 times.append(ev0.elapsed_time(ev1))
+                # products of the profiled precision that ran (not skipped launches)
+                executed += r["hx_products"] if prec == pd.PD_PREC_FP64 else r["iterations_fp32"]
             pkey = "fp64" if prec == pd.PD_PREC_FP64 else "fp32"
             cnt, ms = pd.pairdiag_get_profile(s.h, pd.PD_PREC_FP64 if pkey == "fp64" else pd.PD_PREC_MIXED)
             pd.pairdiag_set_profiling(s.h, False)
             if cnt and pkey not in roof:
                 es = 8 if pkey == "fp64" else 4
                 alg = nnz * es + 2 * dim * es
-                avg_s = ms / cnt * 1e-3
+                avg_s = ms / max(1, executed) * 1e-3
                 roof[pkey] = {"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
                               "frac": alg / avg_s / 1e9 / peak, "peak_kind": peak_kind,
                               "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
-                              "hx_nnz_per_s": nnz / avg_s, "launches": cnt}
+                              "hx_nnz_per_s": nnz / avg_s, "timed_launches": cnt, "executed_products": executed}
         out[name] = {"time_to_e0_ms": statistics.median(times), "iterations": r["iterations"],
                      "iterations_fp32": r["iterations_fp32"], "hx_products": r["hx_products"],
                      "nnz_per_s": r["hx_products"] * nnz / (statistics.median(times) * 1e-3),

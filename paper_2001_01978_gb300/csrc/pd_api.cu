@@ -358,6 +358,9 @@ int lanczos_step(pairdiag *h, int dtype, int i)
 // norm).  On return Q_0 is the normalised best vector.  The host synchronises
 // once per cycle (to test convergence on the restart vector); breakdown inside
 // a cycle is handled on the device.
+// Lanczos steps between two estimates of the cycle's Ritz residual
+constexpr int kRitzCheckEvery = 4;
+
 int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &cs)
 {
     const int64_t dim = h->dim;
@@ -398,6 +401,10 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         for (int i = 1; i < m; ++i) {
             PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));
             PD_TRY(lanczos_step(h, dtype, i));
+            // restarted mode: end the cycle as soon as its lowest Ritz pair is
+            // converged, instead of running the whole window
+            if (h->opt.mode == 0 && (i + 1) % kRitzCheckEvery == 0 && i + 1 < m)
+                PD_CUDA(ritz_estimate_launch(S, i, tol, st));
         }
         PD_CUDA(tridiag_launch(S, 0, st));
         PD_CUDA(ritz_launch(dtype, Q, h->ldq, &S->used, S->s, dim, h->d_part, &S->norm2, st, tk));

@@ -347,6 +347,9 @@ cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, co
                                  const int *skip = nullptr, unsigned long long *ticket = nullptr);
 // start of a cycle: used = 0, broken = 0, tnorm = 0
 cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
+// after step i of a cycle: when the residual of the lowest Ritz pair of the
+// steps so far is within tol of its Ritz value, set broken (the cycle ends)
+cudaError_t ritz_estimate_launch(LanczosScalars *S, int i, double tol, cudaStream_t st);
 // lowest two eigenvalues + lowest eigenvector of tridiag(alpha, beta) -> S->theta, S->s;
 // size m, or S->used when m <= 0
 cudaError_t tridiag_launch(LanczosScalars *S, int m, cudaStream_t st);
