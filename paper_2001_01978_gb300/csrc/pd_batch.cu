@@ -22,6 +22,12 @@
 
 using namespace pd;
 
+namespace pd {
+// pd_lanczos.cu: after step i of a cycle, problems whose lowest Ritz pair of
+// the steps so far meets tol end the cycle (broken and skip set)
+cudaError_t batch_ritz_estimate_launch(BatchState *S, int count, int i, double tol, cudaStream_t st);
+}
+
 namespace {
 
 struct DevBuf {
@@ -263,6 +269,8 @@ extern "C" int pairdiag_batch_ground_state(int count, const int *omega, const in
             for (int i = 1; i < m; ++i) {
                 PD_CUDA(seg_scale_launch(dt, V, pv, q(i), S, i - 1, 0, st));
                 PD_TRY(step(i));
+                // every 4 steps: problems whose Ritz pair meets tol end the cycle
+                if ((i + 1) % 4 == 0 && i + 1 < m) PD_CUDA(batch_ritz_estimate_launch(S, count, i, tol_run, st));
             }
             PD_CUDA(batch_tridiag_launch(S, count, st));
             PD_CUDA(seg_ritz_launch(dt, V, Q, total, S, part, st));

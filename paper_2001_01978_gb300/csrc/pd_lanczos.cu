@@ -451,32 +451,29 @@ __device__ void tridiag_warp(const double *alpha, const double *beta, int m, dou
     __syncwarp();
 }
 
-// Residual of the lowest Ritz pair of the cycle so far (steps 0..i).  With
-// full reorthogonalisation it equals beta_i |s_last|, s the lowest eigenvector
-// of the (i+1) x (i+1) matrix tridiag(alpha, beta) (Algorithm 2), taken here from
-// an FP32 multisection and two inverse-iteration solves.  Once it is within
-// tol of |theta| the rest of the cycle is skipped (broken = 1): the restart
-// from that Ritz vector follows at once, and its |beta_1/alpha_1| decides
-// convergence as before.  One warp.
-__global__ void ritz_estimate_kernel(LanczosScalars *S, int i, double tol)
+// Residual test of the lowest Ritz pair of a cycle so far (steps 0..i).  With
+// full reorthogonalisation the residual equals beta_i |s_last|, s the lowest
+// eigenvector of the (i+1) x (i+1) matrix tridiag(alpha, beta) (Algorithm 2),
+// taken here from an FP32 multisection and two inverse-iteration solves.
+// Returns, in every lane, whether it is within tol of |theta|.  One warp; the
+// work arrays (kMaxWindow doubles each) are shared memory of this warp.
+__device__ bool ritz_converged_warp(const double *alpha, const double *beta, int i, double tol, double *a,
+                                    double *b, double *b2, double *z, double *u0, double *u1, double *u2)
 {
-    __shared__ double a[kMaxWindow], b[kMaxWindow], b2[kMaxWindow], z[kMaxWindow];
-    __shared__ double u0[kMaxWindow], u1[kMaxWindow], u2[kMaxWindow];
-    if (S->broken) return;                        // uniform: breakdown, or already estimated
     const int m = i + 1;
     const int lane = threadIdx.x & 31;
     double scale = 0.0;
     for (int k = 0; k < m; ++k) {
-        const double rad = (k + 1 < m ? fabs(S->beta[k]) : 0.0) + (k > 0 ? fabs(S->beta[k - 1]) : 0.0);
-        scale = fmax(scale, fabs(S->alpha[k]) + rad);
+        const double rad = (k + 1 < m ? fabs(beta[k]) : 0.0) + (k > 0 ? fabs(beta[k - 1]) : 0.0);
+        scale = fmax(scale, fabs(alpha[k]) + rad);
     }
-    if (!(scale > 0.0)) return;
+    if (!(scale > 0.0)) return false;
     const double inv = 1.0 / scale;
     float *af = reinterpret_cast<float *>(u0);
     float *b2f = reinterpret_cast<float *>(u1);
     for (int k = lane; k < m; k += 32) {
-        a[k] = S->alpha[k] * inv;
-        b[k] = (k + 1 < m) ? S->beta[k] * inv : 0.0;
+        a[k] = alpha[k] * inv;
+        b[k] = (k + 1 < m) ? beta[k] * inv : 0.0;
         b2[k] = b[k] * b[k];
         af[k] = (float)a[k];
         b2f[k] = (float)b2[k];
@@ -485,19 +482,49 @@ __global__ void ritz_estimate_kernel(LanczosScalars *S, int i, double tol)
     float lo = -1.25f, hi = 1.25f;
     multisect<float>(af, b2f, m, 1, lo, hi, 4e-7f);
     __syncwarp();
+    int ok = 0;
     if (lane == 0) {
         const double t = 0.5 * ((double)lo + (double)hi);
         for (int k = 0; k < m; ++k) z[k] = 1.0;
-        double nrm = 1.0;
         for (int it = 0; it < 2; ++it) {
             tridiag_solve(a, b, m, t, z, u0, u1, u2, DBL_EPSILON);
-            nrm = 0.0;
+            double nrm = 0.0;
             for (int k = 0; k < m; ++k) nrm += z[k] * z[k];
             nrm = 1.0 / sqrt(nrm);
             for (int k = 0; k < m; ++k) z[k] *= nrm;
         }
-        const double r = S->beta[i] * fabs(z[m - 1]);
-        if (isfinite(r) && r <= tol * fabs(t * scale)) S->broken = 1;
+        const double r = beta[i] * fabs(z[m - 1]);
+        ok = isfinite(r) && r <= tol * fabs(t * scale);
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// After step i of a cycle: once its lowest Ritz pair meets tol the rest of
+// the cycle is skipped (broken = 1); the restart from that Ritz vector follows
+// at once, and its |beta_1/alpha_1| decides convergence as before.  One warp.
+__global__ void ritz_estimate_kernel(LanczosScalars *S, int i, double tol)
+{
+    __shared__ double a[kMaxWindow], b[kMaxWindow], b2[kMaxWindow], z[kMaxWindow];
+    __shared__ double u0[kMaxWindow], u1[kMaxWindow], u2[kMaxWindow];
+    if (S->broken) return;                        // uniform: breakdown, or already converged
+    const bool done = ritz_converged_warp(S->alpha, S->beta, i, tol, a, b, b2, z, u0, u1, u2);
+    if (done && threadIdx.x == 0) S->broken = 1;
+}
+
+// Batched form: one warp per problem still running in the cycle
+__global__ void batch_ritz_estimate_kernel(BatchState *S, int count, int i, double tol)
+{
+    __shared__ double work[4][7][kMaxWindow];
+    const int wi = threadIdx.x >> 5;
+    const int pr = blockIdx.x * 4 + wi;
+    if (pr >= count) return;
+    BatchState &P = S[pr];
+    if (P.skip || P.used != i + 1) return;        // warp-uniform
+    double (*w)[kMaxWindow] = work[wi];
+    const bool done = ritz_converged_warp(P.alpha, P.beta, i, tol, w[0], w[1], w[2], w[3], w[4], w[5], w[6]);
+    if (done && (threadIdx.x & 31) == 0) {
+        P.broken = 1;
+        P.skip = 1;
     }
 }
 
@@ -1118,6 +1145,13 @@ cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st)
 cudaError_t ritz_estimate_launch(LanczosScalars *S, int i, double tol, cudaStream_t st)
 {
     ritz_estimate_kernel<<<1, 32, 0, st>>>(S, i, tol);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_ritz_estimate_launch(BatchState *S, int count, int i, double tol, cudaStream_t st)
+{
+    batch_ritz_estimate_kernel<<<(count + 3) / 4, 128, 0, st>>>(S, count, i, tol);
     count_launches(1);
     return cudaGetLastError();
 }
