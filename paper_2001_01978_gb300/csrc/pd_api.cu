@@ -375,6 +375,8 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     PD_CUDA(multidot_launch(dtype, Q, h->ldq, 1, Q, dim, h->d_part, &S->dots[0], st, nullptr, tk));
     PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
     std::vector<double> history;                  // |beta_1/alpha_1| per cycle
+    bool ended_early = false;                     // the last cycle stopped before the full window
+    double est_tol = tol;                         // threshold of the Ritz estimate
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
         PD_CUDA(cycle_reset_launch(S, st));
         PD_TRY(lanczos_step(h, dtype, 0));
@@ -398,13 +400,17 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
             const size_t nh = history.size();
             if (dtype == 1 && nh >= 4 && fp32_stalled(history[nh - 1], history[nh - 4], tol)) return PD_OK;
         }
+        // the Ritz estimate stopped the last cycle early but the restart test
+        // failed (the estimate was optimistic, e.g. near the rounding floor of
+        // the vectors): later cycles stop only at a 4x smaller estimate
+        if (ended_early) est_tol *= 0.25;
         for (int i = 1; i < m; ++i) {
             PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));
             PD_TRY(lanczos_step(h, dtype, i));
             // restarted mode: end the cycle as soon as its lowest Ritz pair is
             // converged, instead of running the whole window
             if (h->opt.mode == 0 && (i + 1) % kRitzCheckEvery == 0 && i + 1 < m)
-                PD_CUDA(ritz_estimate_launch(S, i, tol, st));
+                PD_CUDA(ritz_estimate_launch(S, i, est_tol, st));
         }
         PD_CUDA(tridiag_launch(S, 0, st));
         PD_CUDA(ritz_launch(dtype, Q, h->ldq, &S->used, S->s, dim, h->d_part, &S->norm2, st, tk));
@@ -415,6 +421,7 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         PD_CUDA(cudaMemcpyAsync(&used, &S->used, sizeof(int), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaStreamSynchronize(st));
         cs.iterations += used - 1;
+        ended_early = used < m;
         if (!std::isfinite(th[0])) return fail(PD_ECUDA, "non-finite Ritz value in cycle %d", cycle);
         cs.energy = th[0];
         cs.gap = th[1] - th[0];
