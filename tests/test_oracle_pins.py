@@ -284,3 +284,33 @@ def test_richardson_random_levels_vs_dense(seed, g):
     G = np.full((omega, omega), g)
     ref = np.linalg.eigvalsh(oracle.dense_matrix(omega, n, e, G))[0]
     assert abs(richardson.ground_energy(e, g, n) - ref) <= 1e-11 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("m", [4, 8, 12])
+def test_ritz_residual_equals_beta_times_last_component(m):
+    """The identity the solver's early end of a cycle relies on: after m Lanczos
+    steps with full reorthogonalisation (Algorithm 2), the residual of the
+    lowest Ritz pair (theta, Q s) of the m x m tridiagonal matrix is
+    beta_m |s_m|.  Checked on the dense matrix of Eq. 2 (Omega=10, N=5) with
+    numpy's eigensolver for the small matrix."""
+    omega, n = 10, 5
+    e, G = pd_inputs.separable_noise(omega, seed=21)
+    A = oracle.dense_matrix(omega, n, e, G)
+    dim = A.shape[0]
+    q = np.random.default_rng(3).standard_normal(dim)
+    Q = [q / np.linalg.norm(q)]
+    alpha, beta = [], []
+    for i in range(m):
+        p = A @ Q[i]
+        a = Q[i] @ p
+        p = p - a * Q[i] - (beta[-1] * Q[i - 1] if i > 0 else 0.0)
+        for _ in range(2):                        # full reorthogonalisation, twice
+            p = p - np.stack(Q).T @ (np.stack(Q) @ p)
+        alpha.append(a)
+        beta.append(np.linalg.norm(p))
+        Q.append(p / beta[-1])
+    T = np.diag(alpha) + np.diag(beta[:-1], 1) + np.diag(beta[:-1], -1)
+    w, S = np.linalg.eigh(T)
+    y = np.stack(Q[:m]).T @ S[:, 0]
+    resid = np.linalg.norm(A @ y - w[0] * y)
+    assert abs(resid - beta[-1] * abs(S[-1, 0])) <= 1e-10 * max(1.0, resid)
