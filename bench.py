@@ -77,6 +77,17 @@ def parse_args():
 
 
 # ----------------------------------------------------------------- helpers --
+def combine_ranks(ms: float, nnz: float, dist, device: str = "cuda"):
+    """Replicas: the slowest rank's time and the nonzeros of all ranks (every
+    rank calls this; the whole-job throughput is their quotient)."""
+    import torch
+    t = torch.tensor([ms, nnz], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -311,11 +322,7 @@ def run_ours(args):
     products = sum(r["hx_products"] for r in results)
     nnz_done = products * nnz
     if dist is not None:
-        t = torch.tensor([total_ms, float(nnz_done)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, nnz_all = float(tmax[0]), float(t[1])
+        total_ms_max, nnz_all = combine_ranks(total_ms, float(nnz_done), dist, "cuda")
     else:
         total_ms_max, nnz_all = total_ms, float(nnz_done)
     value = nnz_all / (total_ms_max * 1e-3)
