@@ -31,7 +31,7 @@ def test_two_replicas_combine_time_and_work():
     with socket.socket() as sk:
         sk.bind(("127.0.0.1", 0))
         port = sk.getsockname()[1]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork: the process may hold CUDA state
         out = m.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         got = dict(out)
