@@ -44,8 +44,9 @@ L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 30 for the benchmark line and the reference arm, 10 for --hx-only, 3 for --warm, 2 for --batch, 1 for --big)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default 3; 1 for --big)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tol", type=float, default=1e-5,
@@ -645,6 +646,12 @@ def run_batch(args):
 
 def main():
     args = parse_args()
+    mode = ("batch" if args.batch else "warm" if args.warm else "big" if args.big else
+            "hx" if args.hx_only and args.impl != "reference" else "line")
+    if args.steps is None:
+        args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10}.get(mode, 30)
+    if args.warmup is None:
+        args.warmup = 1 if mode == "big" else 3
     if args.batch:
         return run_batch(args)
     if args.warm:
