@@ -11,7 +11,10 @@ store them, while every sum stays in FP64; the remaining difference to the GPU
 is then the FP32 accumulation order only.
 
 The backward pass is the chain rule written out; tests pin it against central
-finite differences of ``loss``.
+finite differences of ``loss``.  The paper has no network, so nothing in it pins
+this twin (parity unpinned by the paper): its forward pass is pinned by
+closed-form special cases (an output layer alone, single paths through the
+packed weights and biases), its gradient by finite differences.
 """
 from __future__ import annotations
 

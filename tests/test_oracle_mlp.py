@@ -1,5 +1,8 @@
-"""The FP64 twin of the warm-start network: analytic gradient pinned against
+"""The FP64 twin of the warm-start network: forward pass pinned by closed-form
+special cases, analytic gradient pinned against
 central finite differences (CPU only)."""
+import math
+
 import numpy as np
 
 from oracle import mlp
@@ -32,3 +35,53 @@ def test_bf16_rounding():
     assert r[3] == -3.140625
     assert r[4] == 0.0
     assert r[5] == 1.0078125      # representable
+
+
+def _zero():
+    return [np.zeros(s) for s in mlp.SHAPES]
+
+
+def _silu(z):
+    return z / (1.0 + math.exp(-z))
+
+
+def test_forward_output_layer_closed_form():
+    """All hidden weights zero: A3 = silu(b3) on every row, so out = w4 . silu(b3) + b4.
+    With b3 = (ln 3, 0, -ln 3) and w4 = (1, 1, 1): silu(ln 3) = 3/4 ln 3 and
+    silu(-ln 3) = -1/4 ln 3, so out = 1/2 ln 3 + b4; and the loss against
+    t = out + 2 is 4."""
+    P = _zero()
+    P[5][:3] = [math.log(3.0), 0.0, -math.log(3.0)]
+    P[6][:3] = 1.0
+    P[7][0] = 0.37
+    X = np.random.default_rng(1).normal(size=(5, mlp.F_IN))
+    out, _ = mlp.forward(mlp.pack(P), X)
+    assert np.allclose(out, 0.5 * math.log(3.0) + 0.37, rtol=0, atol=1e-15)
+    assert abs(mlp.loss(mlp.pack(P), X, out + 2.0) - 4.0) < 1e-14
+
+
+def test_forward_single_path_follows_the_packing():
+    """One nonzero weight per layer on the path input 5 -> unit 7 -> unit 3 ->
+    unit 11 -> output (row-major W1[16x128], W2, W3[128x128]): the output is
+    silu(silu(silu(x_5))), computed here with scalar math.  A transposed
+    matrix or a misplaced block of the packing routes the path through a zero."""
+    P = _zero()
+    P[0][5, 7] = 1.0
+    P[2][7, 3] = 1.0
+    P[4][3, 11] = 1.0
+    P[6][11] = 1.0
+    X = np.zeros((3, mlp.F_IN))
+    X[:, 5] = [math.log(3.0), -0.7, 2.5]
+    out, _ = mlp.forward(mlp.pack(P), X)
+    ref = [_silu(_silu(_silu(z))) for z in X[:, 5]]
+    assert np.allclose(out, ref, rtol=1e-15, atol=1e-15)
+    # the same path driven by the biases b1 (unit 7) and b2 (unit 3) instead
+    for layer, unit, down in ((1, 7, None), (3, 3, 0)):
+        Q = [p.copy() for p in P]
+        Q[0][:] = 0.0
+        if down is not None:
+            Q[2][:] = 0.0
+        Q[layer][unit] = 1.25
+        out2, _ = mlp.forward(mlp.pack(Q), np.zeros((1, mlp.F_IN)))
+        expect = _silu(_silu(_silu(1.25))) if layer == 1 else _silu(_silu(1.25))
+        assert abs(out2[0] - expect) < 1e-15, (layer, out2[0], expect)
