@@ -14,6 +14,8 @@ Contents
     equations in their eigenvalue-based form (an independent route, used as a
     pin for the matrix path).
   * ``mlp.py``: the FP64 twin of the warm-start network (forward/backward).
+  * ``odd.py``: odd-mass systems in the blocking approximation (Eq. 3): every
+    blocked subspace solved as a seniority-zero problem on the other orbits.
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against the
 paper's printed values, closed forms, invariants or brute force.
