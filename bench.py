@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--big", action="store_true",
                     help="Omega=32, N=16 (dim 6.0e8): time-to-E0 of FP64, mixed and mixed+learned start")
+    ap.add_argument("--odd", action="store_true",
+                    help="odd-mass twin of the default workload (25 orbits, 12 pairs + 1 particle, Block = 0)")
     ap.add_argument("--warm", action="store_true",
                     help="Omega=30 workload: FP64 random start vs mixed + learned warm start (own JSON line)")
     ap.add_argument("--train-problems", type=int, default=240)
@@ -644,20 +646,62 @@ def run_batch(args):
     return 0
 
 
+def run_odd(args):
+    """Odd-mass twin of the default workload: 25 orbits (separable G plus noise, seed
+    1), 12 pairs and one unpaired particle, every blocked subspace solved (the
+    paper's Block = 0, Eq. 3): 25 subspaces of C(24,12) = 2.7e6 states each.
+    Time to the lowest E_b, plain FP64 vs the mixed form, same tolerance."""
+    import torch
+    import paper_2001_01978_gb300 as pd
+    torch.cuda.set_device(0)
+    omega, n = 25, 12
+    e, G = pd_inputs.separable_noise(omega, seed=1)
+    dim = math.comb(omega - 1, n)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    clocks = ClockSampler(0)
+    for name, prec in (("mixed", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
+        opt = pd.pairdiag_default_options(precision=prec, window=args.window, seed=1)
+        for _ in range(args.warmup):
+            pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, want_vector=False)
+        times, r = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, want_vector=False)
+            times.append((time.perf_counter() - t0) * 1e3)
+        ms = statistics.median(times)
+        out[name] = {"time_to_e0_ms": ms, "ms_per_subspace": ms / omega, "e0": r["e0"], "block": r["block"],
+                     "winner_iterations": r["iterations"], "winner_rel_residual": r["rel_residual"],
+                     "status": r["status"]}
+    clk = clocks.stop()
+    out["mixed"]["e0_rel_diff_vs_fp64"] = abs(out["mixed"]["e0"] - out["fp64"]["e0"]) / abs(out["fp64"]["e0"])
+    print(json.dumps({"odd_mass": True, "workload": "25 orbits, 12 pairs + 1 particle, separable G + noise, seed 1",
+                      "subspaces": omega, "dim_per_subspace": dim, "tol": args.tol, "window": args.window,
+                      "steps": args.steps, "warmup": args.warmup, "timing": "host wall clock around the "
+                      "synchronous call (it solves the subspaces one after another)",
+                      "l2": "flushed between calls", "forms": out, "clocks": clk,
+                      "speedup_mixed_vs_fp64": out["fp64"]["time_to_e0_ms"] / out["mixed"]["time_to_e0_ms"]}))
+    return 0
+
+
 def main():
     args = parse_args()
-    mode = ("batch" if args.batch else "warm" if args.warm else "big" if args.big else
+    mode = ("batch" if args.batch else "warm" if args.warm else "big" if args.big else "odd" if args.odd else
             "hx" if args.hx_only and args.impl != "reference" else "line")
     if args.steps is None:
-        args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10}.get(mode, 30)
+        args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10, "odd": 3}.get(mode, 30)
     if args.warmup is None:
-        args.warmup = 1 if mode == "big" else 3
+        args.warmup = 1 if mode in ("big", "odd") else 3
     if args.batch:
         return run_batch(args)
     if args.warm:
         return run_warm(args)
     if args.big:
         return run_big(args)
+    if args.odd:
+        return run_odd(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

@@ -270,6 +270,42 @@ int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs,
                                 pairdiag_mlp_t *mlp, double *e0, int *status,
                                 pairdiag_batch_result *results, void *stream);
 
+/* ---------------------------------------------------------- odd mass ---- */
+/*
+ * Odd-mass ground state in the blocking approximation (Eq. 3; the paper's
+ * half-integer N_Pairs with its Block argument, Sec. 4.2).  The unpaired
+ * particle occupies orbit b and keeps every pair out of it, so the subspace
+ * with b blocked is the seniority-zero space of n_pairs pairs on the other
+ * omega-1 orbits, and
+ *     E_b = e_b + E0(Eq. 2 with e and G restricted to the orbits i != b).
+ * Each subspace is solved as a handle of this library on the restricted
+ * (e, G), in turn, on the current CUDA device.
+ *   omega, n_pairs : omega in 2..62, n_pairs in 0..omega-1 (2*n_pairs+1 particles)
+ *   e, G           : host, as in pairdiag_create (G exactly symmetric)
+ *   block          : -1 = every b, the lowest E_b is returned (the paper's Block = 0);
+ *                    b in 0..omega-1 = that subspace alone (the paper's Block = b+1)
+ *   tol, opt       : as in pairdiag_ground_state / pairdiag_create; tol is relative to
+ *                    the pair part's Rayleigh quotient, without the constant e_b.
+ *                    PD_START_USER is rejected (there is one vector per subspace)
+ *   mlp            : the warm-start network for PD_START_MLP (else nullable)
+ *   e0             : host, receives E_b of the returned subspace
+ *   block_out      : host, nullable, receives its b
+ *   energies       : host [omega], nullable, E_b of every solved b, NaN for the others
+ *   occ            : host [omega], nullable, N_Occup of the returned state (Sec. 4.3):
+ *                    2<S+_i S-_i> on the paired orbits, 1 on the blocked orbit
+ *   vec            : host [C(omega-1, n_pairs)] doubles, nullable: the returned pair
+ *                    vector, normalised, in the basis of the omega-1 unblocked orbits
+ *                    renumbered 0..omega-2 in their original order
+ *   info           : host, nullable: the returned subspace's solve; seconds covers
+ *                    the whole call
+ * Returns PD_OK, PD_ENOCONV if a solved subspace missed tol (all outputs
+ * filled with the best estimates), or another PD_E* code.  Synchronous.
+ */
+int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e, const double *G, int block,
+                              double tol, const pairdiag_options *opt, pairdiag_mlp_t *mlp,
+                              double *e0, int *block_out, double *energies, double *occ,
+                              double *vec, pairdiag_info *info);
+
 /* --------------------------------------------------------- autotuner ---- */
 /*
  * H*x schedule autotuner (an addition of this library; the paper has a single

@@ -12,7 +12,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libpairdiag.so"
-SOURCES = ["pd_hx.cu", "pd_basis.cu", "pd_lanczos.cu", "pd_api.cu", "pd_batch.cu", "pd_mlp.cu", "pd_pool.cu"]
+SOURCES = ["pd_hx.cu", "pd_basis.cu", "pd_lanczos.cu", "pd_api.cu", "pd_batch.cu", "pd_mlp.cu", "pd_pool.cu",
+           "pd_odd.cu"]
 HEADERS = ["pd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -82,6 +82,9 @@ _SIGNATURES = {
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
                                                    ctypes.POINTER(pairdiag_options), _H, _P, _P, _P, _P]),
+    "pairdiag_odd_ground_state": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.POINTER(pairdiag_options), _H, _P, _P, _P, _P, _P,
+                                                 ctypes.POINTER(pairdiag_info)]),
     "pairdiag_mlp_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_H)]),
     "pairdiag_mlp_destroy": (None, [_H]),
     "pairdiag_mlp_num_params": (ctypes.c_int, []),
@@ -305,6 +308,34 @@ def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | No
     for f, _ in pairdiag_batch_result._fields_:
         out[f] = np.array([getattr(r, f) for r in res])
     return out
+
+
+def pairdiag_odd_ground_state(omega: int, n_pairs: int, e, G, tol: float, block: int = -1,
+                              opt: pairdiag_options | None = None, mlp=None, want_vector: bool = True) -> dict:
+    """Odd-mass ground state with one blocked orbit (block -1: every orbit, the
+    lowest returned).  Returns e0, block, energies [omega] (NaN where not
+    solved), occ [omega], vec (pair vector on the other orbits, or None), the
+    winning subspace's info fields and the call's status."""
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    if e.shape != (omega,) or G.shape != (omega, omega):
+        raise ValueError("e must be [omega] and G [omega, omega]")
+    e0 = ctypes.c_double()
+    b_out = ctypes.c_int()
+    energies = np.empty(omega)
+    occ = np.empty(omega)
+    vec = None
+    if want_vector and 0 <= n_pairs < omega:
+        from math import comb
+        vec = np.empty(comb(omega - 1, n_pairs))
+    info = pairdiag_info()
+    st = _check(lib().pairdiag_odd_ground_state(omega, n_pairs, _np_ptr(e), _np_ptr(G), block, tol,
+                                                ctypes.byref(opt) if opt is not None else None, mlp,
+                                                ctypes.byref(e0), ctypes.byref(b_out), _np_ptr(energies),
+                                                _np_ptr(occ), _np_ptr(vec) if vec is not None else None,
+                                                ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
+    return dict(e0=e0.value, block=b_out.value, energies=energies, occ=occ, vec=vec, status=st,
+                **info.as_dict())
 
 
 def pairdiag_tridiag_lowest(h, alpha, beta):

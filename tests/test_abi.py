@@ -70,3 +70,29 @@ def test_tune_table_host_only(libpath):
     assert pd.pairdiag_tune_get(20, 10, 1) == (0, 0)
     with pytest.raises(pd.PairDiagError):
         pd.pairdiag_tune_set(20, 10, 1, 14, 1)
+
+
+def test_odd_ground_state_argument_errors(libpath):
+    """Argument checks of the odd-mass entry point return PD_EINVAL before any
+    device call."""
+    import numpy as np
+    import paper_2001_01978_gb300 as pd
+    e = np.arange(6.0)
+    G = np.full((6, 6), -0.3)
+    bad = [
+        dict(omega=1, n_pairs=0, e=e[:1], G=G[:1, :1]),        # no orbit left to pair in
+        dict(omega=6, n_pairs=6, e=e, G=G),                    # 13 particles in 6 orbits
+        dict(omega=6, n_pairs=-1, e=e, G=G),
+        dict(omega=6, n_pairs=2, e=e, G=G, block=6),
+        dict(omega=6, n_pairs=2, e=e, G=G, block=-2),
+        dict(omega=6, n_pairs=2, e=e, G=G, tol=-1.0),
+        dict(omega=6, n_pairs=2, e=e, G=G + np.triu(np.full((6, 6), 1e-3), 1)),
+        dict(omega=6, n_pairs=2, e=np.r_[e[:5], np.nan], G=G),
+        dict(omega=6, n_pairs=2, e=e, G=G, opt=pd.pairdiag_default_options(start=pd.PD_START_USER)),
+        dict(omega=6, n_pairs=2, e=e, G=G, opt=pd.pairdiag_default_options(start=pd.PD_START_MLP)),
+    ]
+    for kw in bad:
+        kw.setdefault("tol", 1e-10)
+        with pytest.raises(pd.PairDiagError) as err:
+            pd.pairdiag_odd_ground_state(**kw)
+        assert err.value.code == pd.PD_EINVAL, kw
