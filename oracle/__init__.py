@@ -16,6 +16,8 @@ Contents
   * ``mlp.py``: the FP64 twin of the warm-start network (forward/backward).
   * ``odd.py``: odd-mass systems in the blocking approximation (Eq. 3): every
     blocked subspace solved as a seniority-zero problem on the other orbits.
+  * ``excited.py``: the lowest few eigenpairs (Sec. 3.4) of small problems from
+    the dense matrix.
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against the
 paper's printed values, closed forms, invariants or brute force.
