@@ -182,6 +182,28 @@ int pairdiag_ground_state_dev(pairdiag_t *h, double tol, double *e0, double *vec
                               pairdiag_info *info);
 
 /*
+ * The k lowest eigenpairs ("the first few states" that Sec. 3.4 says are
+ * wanted), one after another: state j is the ground state of the operator
+ * projected against the converged states 0..j-1 (locking): every H*x result
+ * and every restart vector of its Lanczos run is orthogonalised against them.
+ * Each state runs the handle's form (FP64, or mixed with FP64 refinement) to
+ * tol as pairdiag_ground_state does.  State 0 starts from the handle's start
+ * kind; state j > 0 from the counter-based random vector of seed opt.seed + j
+ * (a fresh start for each state, so that a degenerate level yields one state
+ * per copy).
+ *   k        : 1..min(64, dim)
+ *   energies : host [k], in the order found (ascending up to tol)
+ *   vecs_dev : device, nullable, [k * dim] doubles: state j at vecs_dev + j*dim,
+ *              normalised, orthogonal to the earlier states up to tol
+ *   info     : host [k], nullable, one record per state
+ * Later pairdiag_ground_state calls on the handle see the whole space again.
+ * Returns PD_OK, PD_ENOCONV if a state missed tol (all outputs filled), or
+ * another PD_E* code.  Synchronous.
+ */
+int pairdiag_lowest_states_dev(pairdiag_t *h, int k, double tol, double *energies, double *vecs_dev,
+                               pairdiag_info *info);
+
+/*
  * Orbit occupation numbers 2 <v|S+_i S-_i|v> (N_Occup, Sec. 4.3) of a
  * normalised FP64 vector v_dev (device, [dim]); occ: host [omega].  Synchronous.
  */

@@ -136,6 +136,14 @@ struct pairdiag {
     double *d_v64 = nullptr, *d_w64 = nullptr;
     std::vector<double> start;
     std::vector<double> start_w;     // per-orbit weights of a product start vector
+    // converged eigenvectors locked out of the Krylov space (lowest few states):
+    // while n_locked > 0 every H*x result and restart vector is projected
+    // against them
+    int n_locked = 0;
+    int lock_cap = 0;
+    double *d_L64 = nullptr;         // [lock_cap * ldq] FP64 locked vectors
+    float *d_L32 = nullptr;          // their FP32 copies (mixed form)
+    double *d_lockc = nullptr;       // [kMaxWindow] projection coefficients
     pairdiag_mlp *mlp = nullptr;     // network predicting them (PD_START_MLP)
     // optional event timing of H*x launches
     bool profiling = false;
@@ -155,7 +163,8 @@ void free_all(pairdiag *h)
     h->hx_events.clear();
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
-                    h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64};
+                    h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64,
+                    h->d_L64, h->d_L32, h->d_lockc};
     // the blocks go back to the library's cache: no queued kernel may still use
     // them (cudaFree gave the same guarantee by synchronising the device)
     cudaDeviceSynchronize();
@@ -318,6 +327,18 @@ void *qvec(pairdiag *h, int dtype, int i)
     return static_cast<char *>(h->d_Q[dtype]) + es * (size_t)i * (size_t)h->ldq;
 }
 
+// v <- v - L (L^T v) against the locked vectors L (storage type dtype): the
+// projected operator whose lowest eigenpair is the next state
+int lock_project(pairdiag *h, int dtype, void *v, const int *skip)
+{
+    if (h->n_locked == 0) return PD_OK;
+    const void *L = dtype == 0 ? static_cast<const void *>(h->d_L64) : static_cast<const void *>(h->d_L32);
+    PD_CUDA(multidot_launch(dtype, L, h->ldq, h->n_locked, v, h->dim, h->d_part, h->d_lockc, h->st, skip,
+                            &h->d_tk->vec_done));
+    PD_CUDA(update_launch(dtype, L, h->ldq, h->n_locked, h->d_lockc, v, h->dim, h->d_part, nullptr, h->st, skip));
+    return PD_OK;
+}
+
 struct CycleStats {
     int iterations = 0;
     int restarts = 0;
@@ -349,6 +370,7 @@ int lanczos_step(pairdiag *h, int dtype, int i)
     const int64_t ld = h->ldq;
     unsigned long long *tk = &h->d_tk->vec_done;
     PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip, S->c1));
+    if (h->n_locked) PD_TRY(lock_project(h, dtype, p, skip));
     PD_CUDA(recur_project_launch(dtype, Q, ld, i, S, p, dim, h->d_part, S->c2, st, skip, tk));
     PD_CUDA(update_launch(dtype, Q, ld, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip, tk, S, i));
     return PD_OK;
@@ -378,6 +400,11 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     bool ended_early = false;                     // the last cycle stopped before the full window
     double est_tol = tol;                         // threshold of the Ritz estimate
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
+        if (h->n_locked) {                        // restart vector orthogonal to the locked states
+            PD_TRY(lock_project(h, dtype, Q, nullptr));
+            PD_CUDA(multidot_launch(dtype, Q, h->ldq, 1, Q, dim, h->d_part, &S->dots[0], st, nullptr, tk));
+            PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
+        }
         PD_CUDA(cycle_reset_launch(S, st));
         PD_TRY(lanczos_step(h, dtype, 0));
         double ab[2];
@@ -855,6 +882,72 @@ int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ)
     PD_CUDA(occupations_launch(h->B, v_dev, h->d_part, h->rgrid, h->d_S->s, h->st));
     PD_CUDA(cudaMemcpyAsync(occ, h->d_S->s, sizeof(double) * h->omega, cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
+}
+
+int pairdiag_lowest_states_dev(pairdiag_t *h, int k, double tol, double *energies, double *vecs_dev,
+                               pairdiag_info *info)
+{
+    if (!h || !energies) return fail(PD_EINVAL, "null argument");
+    if (k < 1 || k > kMaxWindow || (int64_t)k > h->dim)
+        return fail(PD_EINVAL, "k=%d outside 1..min(%d, dim)", k, kMaxWindow);
+    if (!(tol >= 0.0)) return fail(PD_EINVAL, "tol must be >= 0");
+    PD_CUDA(cudaSetDevice(h->device));
+    const int64_t dim = h->dim, ld = h->ldq;
+    const bool mixed = h->opt.precision == PD_PREC_MIXED;
+    if (h->lock_cap < k || (mixed && !h->d_L32)) {
+        PD_CUDA(cudaStreamSynchronize(h->st));
+        pool_free(h->d_L64);
+        pool_free(h->d_L32);
+        h->d_L64 = nullptr;
+        h->d_L32 = nullptr;
+        h->lock_cap = 0;
+        PD_TRY(dalloc(&h->d_L64, (size_t)k * (size_t)ld));
+        if (mixed) PD_TRY(dalloc(&h->d_L32, (size_t)k * (size_t)ld));
+        h->lock_cap = k;
+    }
+    if (!h->d_lockc) PD_TRY(dalloc(&h->d_lockc, (size_t)kMaxWindow));
+    int status = PD_OK;
+    h->n_locked = 0;
+    // state 0 starts as the handle's options say; every later state from its own
+    // random vector: a start reused after projection has no component left in
+    // the rest of a degenerate eigenspace, so Lanczos would skip its other copies
+    const int start0 = h->opt.start;
+    const uint64_t seed0 = h->opt.seed;
+    auto restore = [&]() {
+        h->n_locked = 0;
+        h->opt.start = start0;
+        h->opt.seed = seed0;
+    };
+    for (int j = 0; j < k; ++j) {
+        if (j > 0) {
+            h->opt.start = PD_START_RANDOM;
+            h->opt.seed = seed0 + (uint64_t)j;
+        }
+        double ej = 0.0;
+        double *slot = h->d_L64 + (size_t)j * (size_t)ld;
+        const int st = ground_state_impl(h, tol, &ej, slot, false, nullptr, info ? &info[j] : nullptr);
+        if (st != PD_OK && st != PD_ENOCONV) {
+            restore();
+            return st;
+        }
+        if (st == PD_ENOCONV) status = PD_ENOCONV;
+        energies[j] = ej;
+        if (h->d_L32) {
+            const cudaError_t ce = convert_launch(1, h->d_L32 + (size_t)j * (size_t)ld, 0, slot, dim, h->st);
+            if (ce != cudaSuccess) {
+                restore();
+                return fail(PD_ECUDA, "convert: %s", cudaGetErrorString(ce));
+            }
+        }
+        h->n_locked = j + 1;
+    }
+    restore();                                    // later ground-state calls see the whole space
+    if (vecs_dev)
+        PD_CUDA(cudaMemcpy2DAsync(vecs_dev, sizeof(double) * (size_t)dim, h->d_L64, sizeof(double) * (size_t)ld,
+                                  sizeof(double) * (size_t)dim, (size_t)k, cudaMemcpyDeviceToDevice, h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    if (status == PD_ENOCONV) return fail(PD_ENOCONV, "a state missed tol %.3g", tol);
     return PD_OK;
 }
 

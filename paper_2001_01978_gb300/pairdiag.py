@@ -74,6 +74,8 @@ _SIGNATURES = {
     "pairdiag_ground_state": (ctypes.c_int, [_H, ctypes.c_double, _P, _P, ctypes.POINTER(pairdiag_info)]),
     "pairdiag_ground_state_dev": (ctypes.c_int, [_H, ctypes.c_double, _P, _P, ctypes.POINTER(pairdiag_info)]),
     "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
+    "pairdiag_lowest_states_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, _P, _P,
+                                                  ctypes.POINTER(pairdiag_info)]),
     "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
@@ -258,6 +260,22 @@ def pairdiag_ground_state_dev(h, tol: float, vec=None) -> dict:
                                                 _dev_ptr(vec, torch.float64) if vec is not None else None,
                                                 ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
     return dict(e0=e0.value, status=st, **info.as_dict())
+
+
+def pairdiag_lowest_states_dev(h, k: int, tol: float, vecs=None) -> dict:
+    """The k lowest eigenpairs by locking.  vecs: optional float64 device tensor of
+    k * dim elements (state j at row j).  Returns energies [k], status and the
+    per-state info records."""
+    import torch
+    if vecs is not None and vecs.numel() < k * pairdiag_dim(h):
+        raise ValueError("vecs must hold k * dim elements")
+    energies = np.empty(max(k, 1))
+    infos = (pairdiag_info * max(k, 1))()
+    st = _check(lib().pairdiag_lowest_states_dev(h, k, tol, _np_ptr(energies),
+                                                 _dev_ptr(vecs, torch.float64) if vecs is not None else None,
+                                                 ctypes.cast(infos, ctypes.POINTER(pairdiag_info))),
+                allow=(PD_OK, PD_ENOCONV))
+    return dict(energies=energies[:k], status=st, info=[i.as_dict() for i in infos][:k])
 
 
 def pairdiag_occupations_dev(h, v, omega: int) -> np.ndarray:
