@@ -18,6 +18,8 @@ Contents
     blocked subspace solved as a seniority-zero problem on the other orbits.
   * ``excited.py``: the lowest few eigenpairs (Sec. 3.4) of small problems from
     the dense matrix.
+  * ``truncation.py``: the truncated space of Sec. 3.5 (histogram cutoff of the
+    diagonal elements) and H*x on it by binary search.
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against the
 paper's printed values, closed forms, invariants or brute force.
@@ -65,6 +67,7 @@ def lib():
         L.orc_diag.restype = dbl; L.orc_diag.argtypes = [u64, i32, P, P]
         L.orc_hx.restype = None; L.orc_hx.argtypes = [i32, P, P, P, i64, P, P]
         L.orc_hx_rows.restype = None; L.orc_hx_rows.argtypes = [i32, P, P, P, i64, P, P, i64, P]
+        L.orc_hx_sub.restype = None; L.orc_hx_sub.argtypes = [i32, P, P, P, i64, P, P]
         L.orc_monopole.restype = None; L.orc_monopole.argtypes = [i32, P, P, P, i64, P, P, P]
         L.orc_jacobi.restype = None; L.orc_jacobi.argtypes = [i32, P, P, P]
         L.orc_lanczos_ground.restype = i32

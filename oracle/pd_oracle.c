@@ -138,6 +138,32 @@ void orc_hx(int omega, const double *e, const double *G, const uint64_t *basis,
     }
 }
 
+/* H*x on a truncated space (Sec. 3.5).  basis lists the kept states in
+ * ascending order; a scattered state missing from it is dropped, so the
+ * operator is the principal submatrix of H on the kept states.  Each kept
+ * target is located by binary search, as the paper does once the space is no
+ * longer complete. */
+void orc_hx_sub(int omega, const double *e, const double *G, const uint64_t *basis,
+                int64_t dim, const double *x, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < dim; ++i) {
+        uint64_t s = basis[i];
+        double acc = orc_diag(s, omega, e, G) * x[i];
+        for (int o = 0; o < omega; ++o) {
+            if (!(s >> o & 1ull)) continue;
+            for (int q = 0; q < omega; ++q) {
+                if (s >> q & 1ull) continue;
+                uint64_t t = (s & ~(1ull << o)) | (1ull << q);
+                int64_t j = orc_search(basis, dim, t);
+                if (j < 0) continue;                 /* excluded by the truncation */
+                acc += G[q * omega + o] * x[j];
+            }
+        }
+        y[i] = acc;
+    }
+}
+
 /* The same product restricted to selected rows: y[r] = (H x)[rows[r]]. */
 void orc_hx_rows(int omega, const double *e, const double *G, const uint64_t *basis,
                  int64_t dim, const double *x, const int64_t *rows, int64_t nrows,
