@@ -96,3 +96,15 @@ def test_odd_ground_state_argument_errors(libpath):
         with pytest.raises(pd.PairDiagError) as err:
             pd.pairdiag_odd_ground_state(**kw)
         assert err.value.code == pd.PD_EINVAL, kw
+
+
+def test_binding_shape_checks_need_no_device(libpath):
+    """The binding rejects mis-shaped host inputs before calling the library."""
+    import numpy as np
+    import paper_2001_01978_gb300 as pd
+    with pytest.raises(ValueError):
+        pd.pairdiag_odd_ground_state(6, 2, np.zeros(5), np.zeros((6, 6)), 1e-10)
+    with pytest.raises(ValueError):
+        pd.pairdiag_odd_ground_state(6, 2, np.zeros(6), np.zeros((6, 5)), 1e-10)
+    with pytest.raises(ValueError):
+        pd.pairdiag_create(6, 2, np.zeros(6), np.zeros((5, 5)))
