@@ -25,10 +25,12 @@
  *   - inputs are copied at create time; the caller keeps ownership of every
  *     buffer it passes.  The handle owns its device memory (basis tables,
  *     Lanczos window) and frees it in pairdiag_destroy.
- *   - threads: a handle serves one call at a time; different handles, the
- *     batch and odd-mass calls, the autotuner's table and the device-memory
- *     cache may be used from several threads at once.  pairdiag_last_error()
- *     is per thread.
+ *   - threads: a solver or network handle serves one call at a time;
+ *     different handles, the batch and odd-mass calls (each with its own
+ *     network, if any), the autotuner's table and the device-memory cache may
+ *     be used from several threads at once.  pairdiag_multidot_noalloc shares
+ *     one scratch array per device (see its entry).  pairdiag_last_error() is
+ *     per thread.
  */
 #ifndef PAIRDIAG_H
 #define PAIRDIAG_H
