@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+import pd_inputs
 from oracle import excited
 from test_oracle_odd import fock_hamiltonian, _pattern, _random_problem
 
@@ -66,3 +67,57 @@ def test_lowest_is_the_lanczos_ground_state():
     assert abs(w[0] - r["e0"]) <= 1e-11 * abs(w[0])
     assert abs(abs(V[:, 0] @ r["vec"]) - 1.0) < 1e-10
     assert w[0] < w[1] <= w[2]
+
+
+def _locked_lanczos(M, locked, start, tol=1e-12, m=20, cycles=200):
+    """A plain model of restarted Lanczos on M projected against the locked
+    vectors (full reorthogonalisation, restart from the lowest Ritz vector)."""
+    q = start.copy()
+    for _ in range(cycles):
+        for l in locked:
+            q -= l * (l @ q)
+        q /= np.linalg.norm(q)
+        Q, a, b = [q], [], []
+        for i in range(m):
+            p = M @ Q[i]
+            for l in locked:
+                p -= l * (l @ p)
+            a.append(Q[i] @ p)
+            p -= a[-1] * Q[i]
+            if i:
+                p -= b[-1] * Q[i - 1]
+            for v in Q:
+                p -= v * (v @ p)
+            beta = np.linalg.norm(p)
+            if i == m - 1 or beta < 1e-13 * max(abs(x) for x in a):
+                break
+            b.append(beta)
+            Q.append(p / beta)
+        T = np.diag(a) + np.diag(b[:len(a) - 1], 1) + np.diag(b[:len(a) - 1], -1)
+        w, S = np.linalg.eigh(T)
+        q = np.array(Q[:len(a)]).T @ S[:, 0]
+        if np.linalg.norm(M @ q - w[0] * q) <= tol * abs(w[0]):
+            break
+    return w[0], q / np.linalg.norm(q)
+
+
+def test_locking_needs_a_fresh_start_per_state():
+    """The reading behind the lowest-states entry point.  On a degenerate level a
+    start vector reused after projection has no component left in the rest of
+    the eigenspace once one copy is locked, so the next solve skips the other
+    copies; a fresh random start per state finds every copy, in order."""
+    omega, n, eps, g, k = 10, 4, 0.5, -0.3, 6
+    M = oracle.dense_matrix(omega, n, np.full(omega, eps), np.full((omega, omega), g))
+    ref = quasispin_levels(omega, n, eps, g)[:k]
+    found = {}
+    for label, seeds in (("reused", [1] * k), ("fresh", list(range(1, k + 1)))):
+        locked, energies = [], []
+        for j in range(k):
+            start = pd_inputs.splitmix_uniform(seeds[j], M.shape[0])
+            ej, v = _locked_lanczos(M, locked, start)
+            energies.append(ej)
+            locked.append(v)
+        found[label] = np.array(energies)
+    assert np.allclose(found["fresh"], ref, rtol=0, atol=1e-10)
+    assert not np.allclose(found["reused"], ref, rtol=0, atol=1e-6)
+    assert found["reused"][2] > ref[2] + 1.0        # jumps to a higher level
