@@ -367,7 +367,9 @@ int pairdiag_tune_get(int omega, int n_pairs, int precision, int *low_bits, int 
  * them to the next handle that needs the same sizes: a loop of create / solve /
  * destroy then allocates once.  The paper has no counterpart (its Fortran
  * allocates host arrays).  When cudaMalloc runs out of memory the cache is
- * emptied once and the allocation retried.
+ * emptied once and the allocation retried.  Other allocators of the process
+ * (PyTorch's caching allocator, for instance) cannot reclaim the cached
+ * blocks themselves: release them before large allocations elsewhere.
  * pairdiag_release_cache returns every cached block to the driver (cudaFree);
  * released_bytes (nullable, host) receives their total size.  Blocks still
  * owned by live handles are not touched.  Thread-safe; always PD_OK.
