@@ -677,6 +677,14 @@ def run_odd(args):
                      "status": r["status"]}
     clk = clocks.stop()
     out["mixed"]["e0_rel_diff_vs_fp64"] = abs(out["mixed"]["e0"] - out["fp64"]["e0"]) / abs(out["fp64"]["e0"])
+    # the oracle's E_b of one subspace (committed by tests/golden/make_golden.py)
+    oracle_b = {}
+    for f in sorted((ROOT / "tests" / "golden").glob(f"omega{omega}_n{n}_sepnoise_s1_odd_b*_e0.txt")):
+        vals = [l.split() for l in f.read_text().splitlines() if l.strip() and not l.startswith("#")]
+        oracle_b[int(f.name.split("_odd_b")[1].split("_")[0])] = float(vals[0][0])
+    for v in out.values():
+        if v["block"] in oracle_b:
+            v["e0_rel_err_vs_oracle"] = abs(v["e0"] - oracle_b[v["block"]]) / abs(oracle_b[v["block"]])
     print(json.dumps({"odd_mass": True, "workload": "25 orbits, 12 pairs + 1 particle, separable G + noise, seed 1",
                       "subspaces": omega, "dim_per_subspace": dim, "tol": args.tol, "window": args.window,
                       "steps": args.steps, "warmup": args.warmup, "timing": "host wall clock around the "

@@ -2,6 +2,7 @@
 inside the test-suite.  Calls only ``oracle/`` (and the seeded inputs).
 
     python tests/golden/make_golden.py omega24_n12_sepnoise_s1
+    python tests/golden/make_golden.py odd:25:12:1:11     # Omega, pairs, seed, blocked orbit
 """
 import sys
 import time
@@ -29,6 +30,27 @@ def ground_state(name: str, window: int = 50, tol: float = 1e-12):
     print(out.read_text())
 
 
+def odd_subspace(omega: int, n: int, seed: int, block: int, window: int = 50, tol: float = 1e-12):
+    """E_b of one blocked subspace (Eq. 3) of the separable workload with `seed`."""
+    from oracle import odd
+    e, G = pd_inputs.separable_noise(omega, seed=seed)
+    t0 = time.time()
+    r = odd.blocked_ground(omega, n, e, G, block=block, tol=tol, window=window, max_restarts=400)
+    dt = time.time() - t0
+    out = HERE / f"omega{omega}_n{n}_sepnoise_s{seed}_odd_b{block}_e0.txt"
+    out.write_text(
+        f"# Odd mass (Eq. 3): {omega} orbits, {n} pairs + 1 particle blocking orbit {block} (0-based);\n"
+        "# e, G = pd_inputs.separable_noise(omega, seed).  Oracle restarted Lanczos on the other\n"
+        f"# orbits, window {window}, |beta_1/alpha_1| <= {tol:g}; written by tests/golden/make_golden.py.\n"
+        "# Columns: E_b converged seconds\n"
+        f"{r['e0']!r} {int(r['converged'])} {dt:.1f}\n")
+    print(out.read_text())
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:]:
-        ground_state(name)
+        if name.startswith("odd:"):
+            omega, n, seed, block = (int(v) for v in name.split(":")[1:])
+            odd_subspace(omega, n, seed, block)
+        else:
+            ground_state(name)

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import pd_inputs
+from conftest import read_golden
 from oracle import odd, richardson
 
 pytestmark = pytest.mark.gpu
@@ -112,3 +113,20 @@ def test_missed_tolerance_still_fills_the_outputs():
     assert r["status"] == pd.PD_ENOCONV
     assert np.all(np.isfinite(r["energies"])) and r["e0"] == r["energies"].min()
     assert 0 <= r["block"] < omega and r["occ"][r["block"]] == 1.0
+
+
+def test_full_size_subspace_matches_the_oracle():
+    """The odd-mass benchmark workload (25 orbits, 12 pairs + 1 particle, separable
+    G, seed 1): the subspace of orbit 11, C(24,12) = 2.7e6 states, in both forms,
+    against the oracle's E_b written by tests/golden/make_golden.py."""
+    row = read_golden("omega25_n12_sepnoise_s1_odd_b11_e0.txt")[0]
+    ref = float(row[0])
+    assert int(row[1]) == 1
+    e, G = pd_inputs.separable_noise(25, seed=1)
+    r = pd.pairdiag_odd_ground_state(25, 12, e, G, 1e-10, block=11, want_vector=False)
+    assert r["status"] == pd.PD_OK and r["block"] == 11
+    assert abs(r["e0"] - ref) <= 1e-10 * abs(ref)
+    r = pd.pairdiag_odd_ground_state(25, 12, e, G, 1e-9, block=11, want_vector=False,
+                                     opt=_opt(precision=pd.PD_PREC_MIXED))
+    assert r["status"] == pd.PD_OK
+    assert abs(r["e0"] - ref) <= 1e-8 * abs(ref)
