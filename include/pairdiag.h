@@ -392,6 +392,16 @@ int64_t pairdiag_kernel_launches(void);
 int pairdiag_set_profiling(pairdiag_t *h, int on);
 int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms);
 
+/*
+ * Fused multiply-add throughput of the current device in the arithmetic of
+ * one H*x nonzero (PD_PREC_FP64: FP64 FMA; PD_PREC_MIXED: FP32 FMA): a kernel of
+ * independent FMA chains on every SM, timed with CUDA events on `stream` after
+ * a warm-up launch (median of `reps` launches).  *tflops = 2 x FMAs / second
+ * / 1e12.  The paper has no counterpart; it is the ALU roof of the FP64 H*x
+ * product, which executes one FMA per nonzero.  Synchronous.
+ */
+int pairdiag_fma_peak(int precision, int reps, void *stream, double *tflops);
+
 /* ------------------------------------------------ test hooks (device) ---- */
 
 /*

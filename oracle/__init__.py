@@ -5,8 +5,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 (``paper_2001_01978_gb300``) and neither imports the other.
 
 Contents
-  * ``pd_oracle.c`` (loaded through ctypes): binomials (Eq. extcmn), the '01'
-    inversion successor (Algorithm 1), the basis (Sec. 3.1), binary search and
+  * ``pd_oracle.c`` (loaded through ctypes): binomials (Eq. extcmn), the
+    successor of k-subsets in colexicographic order (Knuth's Algorithm L), the
+    basis in the order of Sec. 3.1, binary search and
     the hash (Sec. 3.2), the diagonal element (Eq. diagonal), H*x by explicit
     scattering (Sec. 3.3), restarted Lanczos with full reorthogonalisation
     (Algorithm 2, Sec. 3.4), cyclic Jacobi.
@@ -90,12 +91,14 @@ def binom(n: int, m: int) -> int:
 
 
 def next_state(s: int) -> int:
-    """Algorithm 1 ('01' inversion) successor."""
+    """Next larger word with the same popcount (the order of Sec. 3.1), by the
+    textbook successor of k-subsets in colexicographic order (Knuth, TAOCP 4A,
+    Sec. 7.2.1.3, Algorithm L)."""
     return int(lib().orc_next_state(s))
 
 
 def basis(omega: int, n: int) -> np.ndarray:
-    """Ascending basis of all omega-bit words with n set bits (Algorithm 1)."""
+    """Ascending basis of all omega-bit words with n set bits (Sec. 3.1, Table 1)."""
     dim = binom(omega, n)
     out = np.zeros(dim, dtype=np.uint64)
     got = lib().orc_build_basis(omega, n, _p(out))

@@ -5,8 +5,9 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
  * benchmark's CPU-baseline leg load this library.  It shares no code with the
- * CUDA path: it follows the paper's own route step by step -- the '01'
- * inversion successor (Algorithm 1) for the basis, binary search (Sec. 3.2)
+ * CUDA path.  Its route: the basis in the order of Sec. 3.1 (ascending
+ * integers, Table 1), generated by the textbook successor of k-subsets in
+ * colexicographic order; binary search (Sec. 3.2)
  * to locate each scattered state, the explicit diagonal (Eq. "diagonal") and
  * off-diagonal elements (Sec. 3.3), Lanczos (Algorithm 2) with full
  * Gram-Schmidt reorthogonalisation and restart from the ground Ritz vector
@@ -37,29 +38,36 @@ uint64_t orc_binom(int n, int m)
     return row[m];
 }
 
-/* Algorithm 1, the '01' inversion: scan upward from bit 0 for the first set
- * bit whose next-higher bit is clear; move that bit up by one place and drop
- * every set bit met below it to the bottom of the word.  Bits are scanned for
- * i = 0, 1, ..., 61 (every bit; the printed loop header's step is read as a
- * typo, since the worked example of Sec. 3.1 needs every bit). */
+/* Successor of a basis state: the next larger word with the same number of
+ * set bits.  A state with N pairs is the subset {c_1 < c_2 < ... < c_N} of its
+ * occupied orbits, and ascending integer order (Sec. 3.1, Table 1) is the
+ * colexicographic order of these subsets.  Its successor is the textbook rule
+ * for stepping through combinations in that order (D. E. Knuth, The Art of
+ * Computer Programming, Vol. 4A, Sec. 7.2.1.3, Algorithm L, "lexicographic
+ * combinations" of the reversed sequence c_N ... c_1): take the smallest j
+ * for which c_j + 1 is not c_{j+1} (with c_{N+1} taken as 64, above every
+ * orbit), raise c_j by one and put c_1 .. c_{j-1} back at 0 .. j-2.
+ * Returns 0 when no successor fits in 64 bits (and for s = 0). */
 uint64_t orc_next_state(uint64_t s)
 {
-    uint64_t moved = 0;                 /* ones collected below the '01' pair */
-    for (int i = 0; i <= 61; ++i) {
-        uint64_t bit = 1ull << i;
-        if (!(s & bit)) continue;
-        s &= ~bit;                      /* take the one at bit i away */
-        if (!(s & (bit << 1))) {        /* bit i+1 clear: the '01' pattern */
-            s |= bit << 1;
-            break;
-        }
-        moved = (moved << 1) | 1ull;    /* another one to refill from bit 0 */
-    }
-    return s + moved;
+    int c[65];
+    int n = 0;
+    for (int p = 0; p < 64; ++p)        /* the occupied orbits, ascending */
+        if (s >> p & 1ull) c[n++] = p;
+    if (n == 0) return 0;
+    c[n] = 64;
+    int j = 0;
+    while (j < n && c[j] + 1 == c[j + 1]) ++j;
+    if (c[j] + 1 >= 64) return 0;       /* the last word of 64-bit states */
+    c[j] += 1;
+    for (int i = 0; i < j; ++i) c[i] = i;
+    uint64_t t = 0;
+    for (int i = 0; i < n; ++i) t |= 1ull << c[i];
+    return t;
 }
 
 /* Sec. 3.1: the basis is every Omega-bit word with N set bits, in ascending
- * order, produced by Algorithm 1 from the minimum 2^N-1 up to the maximum
+ * order, produced by the successor above from the minimum 2^N-1 up to the maximum
  * (2^N-1) << (Omega-N).  Returns the number written (C(Omega,N)). */
 int64_t orc_build_basis(int omega, int n, uint64_t *out)
 {

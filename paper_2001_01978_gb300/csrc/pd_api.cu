@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -212,7 +213,10 @@ int build_tables(pairdiag *h)
         const int64_t dn = (k > 0 && H - ph > 0) ? (H - ph) * (int64_t)host_binom(L, k - 1) : 0;
         max_stage = (int)std::max<int64_t>(max_stage, up + dn);
     }
-    if (nblocks > (int64_t)1 << 31) return fail(PD_ENOTSUP, "too many basis blocks (%lld)", (long long)nblocks);
+    // the persistent H*x kernels keep block indices in int, and their counters
+    // run past nblocks by up to two per CTA before every CTA has stopped
+    if (nblocks > (int64_t)INT_MAX - (int64_t)(1 << 20))
+        return fail(PD_ENOTSUP, "too many basis blocks (%lld)", (long long)nblocks);
     std::vector<uint64_t> hw;
     hw.reserve((size_t)nblocks);
     for (int k = kmin; k <= kmax; ++k) words_with_popcount(H, N - k, hw);
@@ -1065,6 +1069,82 @@ int pairdiag_tune_get(int omega, int n_pairs, int precision, int *low_bits, int 
     if (!low_bits || !hx_variant_) return fail(PD_EINVAL, "null argument");
     if (!tuned_schedule(omega, n_pairs, precision, low_bits, hx_variant_)) { *low_bits = 0; *hx_variant_ = 0; }
     return PD_OK;
+}
+
+}  // extern "C"
+
+// ---- FMA throughput microbenchmark ---------------------------------------------
+namespace {
+
+constexpr int kFmaChains = 8;        // independent chains per thread
+constexpr int kFmaIters = 4096;      // FMAs per chain
+
+// x <- x a + b on kFmaChains independent chains; a = 1 - 2^-20 and b small keep
+// every value bounded.  The sum is stored only when it equals an impossible
+// value, so nothing is written and nothing can be optimised away.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(T a, T b, T *sink)
+{
+    T x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = T(threadIdx.x + c) * T(1e-3);
+    for (int i = 0; i < kFmaIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    if (s == T(-1.25e30)) *sink = s;
+}
+
+template <typename T>
+int fma_peak_t(int reps, cudaStream_t st, double *tflops)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    PD_CUDA(cudaGetDevice(&dev));
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel<T>, 256, 0));
+    const int grid = sms * std::max(1, per_sm) * 4;
+    T *sink = nullptr;
+    PD_CUDA(cudaMalloc(&sink, sizeof(T)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> ms(reps);
+    int rc = PD_OK;
+    const T a = T(1) - T(1) / T(1 << 20), b = T(1e-6);
+    fma_peak_kernel<T><<<grid, 256, 0, st>>>(a, b, sink);            // warm-up
+    count_launches(1);
+    for (int r = 0; r < reps && rc == PD_OK; ++r) {
+        cudaEventRecord(e0, st);
+        fma_peak_kernel<T><<<grid, 256, 0, st>>>(a, b, sink);
+        count_launches(1);
+        cudaEventRecord(e1, st);
+        const cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) rc = fail(PD_ECUDA, "fma_peak: %s", cudaGetErrorString(ce));
+        else cudaEventElapsedTime(&ms[r], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (rc != PD_OK) return rc;
+    std::sort(ms.begin(), ms.end());
+    const double fmas = (double)grid * 256.0 * kFmaChains * kFmaIters;
+    *tflops = 2.0 * fmas / (ms[reps / 2] * 1e-3) / 1e12;
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pairdiag_fma_peak(int precision, int reps, void *stream, double *tflops)
+{
+    if (!tflops || reps < 1) return fail(PD_EINVAL, "bad argument");
+    if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED) return fail(PD_EINVAL, "bad precision");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return precision == PD_PREC_FP64 ? fma_peak_t<double>(reps, st, tflops) : fma_peak_t<float>(reps, st, tflops);
 }
 
 // ---------------------------------------------------------------------------

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_lowest_states_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, _P, _P,
                                                   ctypes.POINTER(pairdiag_info)]),
+    "pairdiag_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
@@ -203,22 +204,31 @@ def pairdiag_basis(h) -> np.ndarray:
 
 def pairdiag_basis_dev(h, first: int, count: int, out) -> None:
     import torch
+    if out.numel() < count:
+        raise ValueError(f"out has {out.numel()} elements, fewer than count = {count}")
     _check(lib().pairdiag_basis_dev(h, first, count, _dev_ptr(out, torch.int64)))
 
 
 def pairdiag_rank_dev(h, states, ranks) -> None:
     import torch
+    if ranks.numel() < states.numel():
+        raise ValueError(f"ranks has {ranks.numel()} elements, fewer than the {states.numel()} states")
     _check(lib().pairdiag_rank_dev(h, _dev_ptr(states, torch.int64), states.numel(), _dev_ptr(ranks, torch.int64)))
 
 
 def pairdiag_hx_dev(h, precision: int, x, y) -> None:
     import torch
     dt = torch.float64 if precision == PD_PREC_FP64 else torch.float32
+    dim = pairdiag_dim(h)
+    if x.numel() < dim or y.numel() < dim:
+        raise ValueError(f"x and y need dim = {dim} elements")
     _check(lib().pairdiag_hx_dev(h, precision, _dev_ptr(x, dt), _dev_ptr(y, dt)))
 
 
 def pairdiag_hx(h, x) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.size != pairdiag_dim(h):
+        raise ValueError("x must hold dim elements")
     y = np.empty_like(x)
     _check(lib().pairdiag_hx(h, _np_ptr(x), _np_ptr(y)))
     return y
@@ -233,6 +243,8 @@ def pairdiag_monopole(h):
 
 def pairdiag_set_start(h, v) -> None:
     v = np.ascontiguousarray(v, dtype=np.float64)
+    if v.size != pairdiag_dim(h):
+        raise ValueError("v must hold dim elements")
     _check(lib().pairdiag_set_start(h, _np_ptr(v)))
 
 
@@ -256,6 +268,8 @@ def pairdiag_ground_state_dev(h, tol: float, vec=None) -> dict:
     import torch
     e0 = ctypes.c_double()
     info = pairdiag_info()
+    if vec is not None and vec.numel() < pairdiag_dim(h):
+        raise ValueError("vec must hold dim elements")
     st = _check(lib().pairdiag_ground_state_dev(h, tol, ctypes.byref(e0),
                                                 _dev_ptr(vec, torch.float64) if vec is not None else None,
                                                 ctypes.byref(info)), allow=(PD_OK, PD_ENOCONV))
@@ -281,14 +295,52 @@ def pairdiag_lowest_states_dev(h, k: int, tol: float, vecs=None) -> dict:
 def pairdiag_occupations_dev(h, v, omega: int) -> np.ndarray:
     """Occupation numbers 2<v|S+_i S-_i|v> of the first ``omega`` orbits."""
     import torch
+    if v.numel() < pairdiag_dim(h):
+        raise ValueError("v must hold dim elements")
     out = np.empty(64, dtype=np.float64)
     _check(lib().pairdiag_occupations_dev(h, _dev_ptr(v, torch.float64), _np_ptr(out)))
     return out[:omega].copy()
 
 
-def pairdiag_multidot(h, Q, ld: int, m: int, p, n: int) -> np.ndarray:
+def _multidot_args(Q, ld: int, m: int, p, n: int, out=None) -> int:
+    """Checks the sizes and types of a multi-dot before any pointer reaches the
+    library, which cannot see them: Q holds m vectors of n elements at stride
+    ld, p holds n elements, out (when given) m float64 values on Q's device.
+    Returns the library's dtype code (0 double, 1 float)."""
     import torch
-    dtype = 0 if Q.dtype == torch.float64 else 1
+    if Q.dtype not in (torch.float64, torch.float32):
+        raise TypeError(f"Q must be float64 or float32, got {Q.dtype}")
+    if p.dtype != Q.dtype:
+        raise TypeError(f"p must have Q's dtype {Q.dtype}, got {p.dtype}")
+    if m < 1 or n < 0 or ld < n:
+        raise ValueError(f"need m >= 1 and 0 <= n <= ld (m={m}, n={n}, ld={ld})")
+    if Q.numel() < (m - 1) * ld + n:
+        raise ValueError(f"Q has {Q.numel()} elements, fewer than (m-1)*ld+n = {(m - 1) * ld + n}")
+    if p.numel() < n:
+        raise ValueError(f"p has {p.numel()} elements, fewer than n = {n}")
+    if p.device != Q.device:
+        raise ValueError("p must be on Q's device")
+    if out is not None:
+        if out.dtype != torch.float64:
+            raise TypeError(f"out must be float64, got {out.dtype}")
+        if out.numel() < m:
+            raise ValueError(f"out has {out.numel()} elements, fewer than m = {m}")
+        if out.device != Q.device:
+            raise ValueError("out must be on Q's device")
+    return 0 if Q.dtype == torch.float64 else 1
+
+
+def pairdiag_fma_peak(precision: int, reps: int = 5, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s, 2 flops per FMA) of the current device in
+    FP64 (PD_PREC_FP64) or FP32 (PD_PREC_MIXED)."""
+    out = ctypes.c_double()
+    sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().pairdiag_fma_peak(precision, reps, ctypes.c_void_p(sp), ctypes.byref(out)))
+    return out.value
+
+
+def pairdiag_multidot(h, Q, ld: int, m: int, p, n: int) -> np.ndarray:
+    dtype = _multidot_args(Q, ld, m, p, n)
     out = np.empty(m, dtype=np.float64)
     _check(lib().pairdiag_multidot(h, dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n, _np_ptr(out)))
     return out
@@ -298,7 +350,7 @@ def pairdiag_multidot_noalloc(Q, ld: int, m: int, p, n: int, out, stream=None) -
     """Allocation-free multi-dot (no handle): out[j] = Q[j] . p in FP64, written to
     the device tensor ``out`` (float64, m elements) on ``stream``."""
     import torch
-    dtype = 0 if Q.dtype == torch.float64 else 1
+    dtype = _multidot_args(Q, ld, m, p, n, out)
     sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().pairdiag_multidot_noalloc(dtype, _dev_ptr(Q), ld, m, _dev_ptr(p, Q.dtype), n,
                                            _dev_ptr(out, torch.float64), ctypes.c_void_p(sp)))
@@ -460,14 +512,18 @@ def pairdiag_set_start_weights(h, w) -> None:
 
 def pairdiag_product_fit(h, v, omega: int) -> np.ndarray:
     import torch
-    w = np.empty(omega, dtype=np.float64)
+    if v.numel() < pairdiag_dim(h):
+        raise ValueError("v must hold dim elements")
+    w = np.empty(64, dtype=np.float64)
     _check(lib().pairdiag_product_fit(h, _dev_ptr(v, torch.float64), _np_ptr(w)))
-    return w
+    return w[:omega].copy()
 
 
 def pairdiag_product_start_dev(h, w, v) -> None:
     import torch
     w = np.ascontiguousarray(w, dtype=np.float64)
+    if v.numel() < pairdiag_dim(h):
+        raise ValueError("v must hold dim elements")
     _check(lib().pairdiag_product_start_dev(h, _np_ptr(w), _dev_ptr(v, torch.float64)))
 
 

@@ -3,6 +3,7 @@ inside the test-suite.  Calls only ``oracle/`` (and the seeded inputs).
 
     python tests/golden/make_golden.py omega24_n12_sepnoise_s1
     python tests/golden/make_golden.py odd:25:12:1:11     # Omega, pairs, seed, blocked orbit
+    python tests/golden/make_golden.py batch:4096:5       # problem count, seed
 """
 import sys
 import time
@@ -47,9 +48,43 @@ def odd_subspace(omega: int, n: int, seed: int, block: int, window: int = 50, to
     print(out.read_text())
 
 
+def batch_picks(count: int, seed: int):
+    """Stratified picks of the mean-field batch workload (12 problems at evenly
+    spaced ranks of the dimension); the oracle's E0 of every pick with
+    dim > 20000, which the test-suite cannot afford to compute itself."""
+    import math
+
+    import numpy as np
+    probs = pd_inputs.batch_workload(count, seed=seed)
+    dims = np.array([math.comb(om, n) for om, n, _, _ in probs])
+    order = np.argsort(dims, kind="stable")
+    picks = [int(order[k]) for k in np.linspace(0, len(order) - 1, 12).astype(int)]
+    lines = []
+    for i in picks:
+        om, n, e, G = probs[i]
+        if dims[i] <= 20000:
+            continue
+        t0 = time.time()
+        r = oracle.lanczos_ground(om, n, e, G, window=50, tol=1e-12, max_restarts=400)
+        dt = time.time() - t0
+        lines.append(f"{i} {om} {n} {dims[i]} {r['e0']!r} {r['rel_residual']!r} {int(r['converged'])} {dt:.1f}")
+        print(lines[-1], flush=True)
+    out = HERE / f"batch{count}_s{seed}_picks_e0.txt"
+    out.write_text(
+        f"# Mean-field batch workload: pd_inputs.batch_workload({count}, seed={seed}); stratified picks\n"
+        "# (12 evenly spaced ranks of dim, stable argsort), those with dim > 20000.  Oracle restarted\n"
+        "# Lanczos (Algorithm 2, full reorthogonalisation, e_1 start), window 50, |beta_1/alpha_1| <= 1e-12;\n"
+        "# written by tests/golden/make_golden.py.\n"
+        "# Columns: problem omega n_pairs dim E0 rel_residual converged seconds\n" + "\n".join(lines) + "\n")
+    print(out.read_text())
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:]:
-        if name.startswith("odd:"):
+        if name.startswith("batch:"):
+            count, seed = (int(v) for v in name.split(":")[1:])
+            batch_picks(count, seed)
+        elif name.startswith("odd:"):
             omega, n, seed, block = (int(v) for v in name.split(":")[1:])
             odd_subspace(omega, n, seed, block)
         else:

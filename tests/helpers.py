@@ -30,3 +30,4 @@ def hx_bound(omega, n, scale, eps):
 
 def comb(omega, n):
     return math.comb(omega, n)
+

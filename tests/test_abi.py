@@ -108,3 +108,29 @@ def test_binding_shape_checks_need_no_device(libpath):
         pd.pairdiag_odd_ground_state(6, 2, np.zeros(6), np.zeros((6, 5)), 1e-10)
     with pytest.raises(ValueError):
         pd.pairdiag_create(6, 2, np.zeros(6), np.zeros((5, 5)))
+
+
+def test_multidot_wrappers_check_sizes_before_any_call():
+    """The library cannot see buffer sizes, so the binding rejects a short out,
+    Q or p and any dtype other than float32/float64 before a pointer is passed
+    (CPU tensors: nothing reaches the library or a GPU)."""
+    torch = pytest.importorskip("torch")
+    import paper_2001_01978_gb300 as pd
+    Q = torch.zeros(3, 8, dtype=torch.float64)
+    p = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError, match="out has 2 elements"):
+        pd.pairdiag_multidot_noalloc(Q, 8, 3, p, 8, torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="Q has 24 elements"):
+        pd.pairdiag_multidot_noalloc(Q, 9, 3, p, 8, torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="p has 7 elements"):
+        pd.pairdiag_multidot_noalloc(Q, 8, 3, p[:7], 8, torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(TypeError, match="float64 or float32"):
+        pd.pairdiag_multidot_noalloc(Q.to(torch.float16), 8, 3, p.to(torch.float16), 8,
+                                     torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(TypeError, match="out must be float64"):
+        pd.pairdiag_multidot_noalloc(Q, 8, 3, p, 8, torch.zeros(3, dtype=torch.float32))
+    with pytest.raises(ValueError, match="Q has 24 elements"):
+        pd.pairdiag_multidot(None, Q, 8, 4, p, 8)
+    # sizes that fit pass the checks and stop at the device check
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        pd.pairdiag_multidot_noalloc(Q, 8, 3, p, 8, torch.zeros(3, dtype=torch.float64))

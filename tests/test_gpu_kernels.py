@@ -32,8 +32,9 @@ def _solver(omega, n, e=None, G=None, **opt):
 
 
 # ------------------------------------------------------------------ basis ---
-@pytest.mark.parametrize("omega", [1, 2, 4, 7, 12, 13, 16])
+@pytest.mark.parametrize("omega", range(1, 25))
 def test_basis_bit_exact_small(omega):
+    """Every (Omega <= 24, N): the whole GPU basis equals the oracle's, word for word."""
     for n in range(omega + 1):
         s, _, _ = _solver(omega, n)
         with s:
@@ -66,6 +67,36 @@ def test_basis_sampled_large(omega, n):
             for j in range(0, cnt, 97):
                 assert bin(int(w[j])).count("1") == n
                 assert oracle.hash_index(int(w[j])) == first + j + 1
+
+
+def _random_states(omega, n, count, seed):
+    """Uniformly random Omega-bit words with n set bits (numpy, no ranking)."""
+    rng = np.random.default_rng(seed)
+    words = np.zeros(count, dtype=np.uint64)
+    for i in range(count):
+        for p in rng.choice(omega, size=n, replace=False):
+            words[i] |= np.uint64(1) << np.uint64(int(p))
+    return words
+
+
+@pytest.mark.parametrize("omega,n", [(12, 6), (20, 9), (24, 12), (32, 16), (38, 10), (50, 5), (62, 31), (62, 1)])
+def test_rank_vs_oracle_hash(omega, n):
+    """pairdiag_rank_dev on random states equals the oracle's hash f - 1 (Sec. 3.2),
+    bit for bit, including the first and last states of the basis."""
+    words = _random_states(omega, n, 4000, seed=omega * 64 + n)
+    lo = (1 << n) - 1
+    words[:2] = [lo, lo << (omega - n)]
+    expect = np.array([oracle.hash_index(int(w)) - 1 for w in words], dtype=np.uint64)
+    e, G = pd_inputs.separable_noise(omega, seed=2)
+    h = pd.pairdiag_create(omega, n, e, G)
+    try:
+        states = torch.from_numpy(words.view(np.int64)).cuda()
+        ranks = torch.empty_like(states)
+        pd.pairdiag_rank_dev(h, states, ranks)
+        got = ranks.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, expect), np.flatnonzero(got != expect)[:5]
+    finally:
+        pd.pairdiag_destroy(h)
 
 
 @pytest.mark.parametrize("omega,n", [(20, 9), (32, 16), (50, 5)])

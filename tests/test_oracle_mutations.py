@@ -17,7 +17,7 @@ MUTATIONS = {
     "diag_drops_self_energy": ("2.0 * e[p] + G[p * omega + p]", "2.0 * e[p]"),
     "diag_single_e": ("2.0 * e[p] + G[p * omega + p]", "e[p] + G[p * omega + p]"),
     "hash_wrong_orbit_offset": ("f += orc_binom(O - 1, j);", "f += orc_binom(O, j);"),
-    "successor_no_refill": ("return s + moved;", "return s;"),
+    "successor_no_refill": ("for (int i = 0; i < j; ++i) c[i] = i;", "for (int i = 0; i < j; ++i) c[i] = c[i];"),
     "offdiag_wrong_sign": ("acc += G[q * omega + o] * x[j];", "acc -= G[q * omega + o] * x[j];"),
     "jacobi_wrong_rotation_sign": ("A[k * n + p] = c * akp - s * akq;", "A[k * n + p] = c * akp + s * akq;"),
 }

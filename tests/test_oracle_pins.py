@@ -14,7 +14,7 @@ from conftest import read_golden
 
 # ----------------------------------------------------------------- basis -----
 def test_table1_basis_and_walk():
-    """Table 1 (Sec. 3.1) and the Algorithm 1 walk 0011->0101->...->1100."""
+    """Table 1 (Sec. 3.1) and the successor walk 0011->0101->...->1100 of Sec. 3.1."""
     rows = read_golden("table1_basis_c4_2.txt")
     expect = [int(r[1]) for r in rows]
     assert list(oracle.basis(4, 2)) == expect
@@ -32,7 +32,7 @@ def test_hash_examples():
 
 @pytest.mark.parametrize("omega", range(1, 17))
 def test_basis_brute_force(omega):
-    """The '01' inversion enumerates exactly the popcount-N words, ascending."""
+    """The successor enumerates exactly the popcount-N words, ascending."""
     words = np.arange(1 << omega, dtype=np.uint64)
     pc = np.array([bin(int(w)).count("1") for w in words])
     for n in range(0, omega + 1):
