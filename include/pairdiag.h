@@ -123,17 +123,24 @@ void pairdiag_destroy(pairdiag_t *h);
 /* Run the handle's kernels on this CUDA stream (cudaStream_t passed as void*). */
 int pairdiag_set_stream(pairdiag_t *h, void *stream);
 
-/* Dimension C(Omega,N) (Eq. extcmn) and off-diagonal count (Sec. 5.3). */
+/* Dimension of the space the solver works in, C(Omega,N) (Eq. extcmn) or the
+ * kept states of a truncation (pairdiag_truncate), and the off-diagonal
+ * nonzeros of the matrix there (Sec. 5.3).  Every vector of the ABI has
+ * pairdiag_dim elements. */
 int64_t pairdiag_dim(const pairdiag_t *h);
 int64_t pairdiag_nnz(const pairdiag_t *h);
+/* C(Omega,N), whether or not the handle is truncated. */
+int64_t pairdiag_full_dim(const pairdiag_t *h);
 
 /*
  * Basis states with indices [first, first+count) (Sec. 3.1, Table 1), written
  * as uint64 words to out_dev (device, [count]).  Bit-exact.  Asynchronous.
+ * The basis, the ranks and pairdiag_monopole always describe the full space
+ * of C(Omega,N) states, also on a truncated handle.
  */
 int pairdiag_basis_dev(const pairdiag_t *h, int64_t first, int64_t count, uint64_t *out_dev);
 
-/* The whole basis into host memory out (host, [dim]).  Synchronous. */
+/* The whole basis into host memory out (host, [C(Omega,N)]).  Synchronous. */
 int pairdiag_basis(const pairdiag_t *h, uint64_t *out);
 
 /*
@@ -161,6 +168,37 @@ int pairdiag_hx(pairdiag_t *h, const double *x, double *y);
  * diagonal elements and the lowest index attaining the minimum.  Synchronous.
  */
 int pairdiag_monopole(pairdiag_t *h, double *dmin, double *dmax, int64_t *pos_min);
+
+/*
+ * Truncated model space (Sec. 3.5, the paper's Dimension_Limit).  When
+ * C(Omega,N) exceeds dimension_limit, the handle keeps only the states of
+ * lowest diagonal element: every diagonal element (Eq. "diagonal", summed
+ * in FP64 over the occupied orbits in ascending order) falls into one of
+ * `bins` equal bins between the smallest and the largest,
+ *     bin = min(floor((D - min) / (max - min) * bins), bins - 1)   (FP64),
+ * and every state whose bin is at most the lowest bin at which the running
+ * count from the bottom reaches dimension_limit is kept (so at least
+ * dimension_limit states; whole bins).  A hop to a dropped state contributes
+ * nothing: H on the kept states is the principal submatrix.
+ *   dimension_limit : >= 1 to truncate; 0 restores the full space
+ *   bins            : 1 .. 2^40; 0 = the paper's 10^8
+ *   kept_dim        : host, receives the new pairdiag_dim
+ * There is no truncation when C(Omega,N) <= dimension_limit or when every
+ * diagonal element is equal.  After the call every vector of the ABI
+ * (pairdiag_hx*, the ground and lowest states, pairdiag_set_start,
+ * pairdiag_occupations_dev) holds the kept states in basis order; a start
+ * vector set earlier is forgotten; PD_START_HF starts from the kept index of
+ * the lowest state.  pairdiag_product_fit is not supported on a truncated
+ * handle (PD_ENOTSUP).  The handle keeps C(Omega,N) int32 kept indices in
+ * device memory.  Synchronous.
+ */
+int pairdiag_truncate(pairdiag_t *h, int64_t dimension_limit, int64_t bins, int64_t *kept_dim);
+
+/* The kept index of every state of a truncated handle: map_dev (device,
+ * int32 [C(Omega,N)]) receives the position of state r among the kept states,
+ * or -1 when it is dropped.  PD_EINVAL when no truncation is active.
+ * Asynchronous. */
+int pairdiag_kept_map_dev(const pairdiag_t *h, int32_t *map_dev);
 
 /*
  * Start vector for PD_START_USER: host [dim] doubles (copied).  Synchronous.

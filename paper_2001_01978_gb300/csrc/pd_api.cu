@@ -112,7 +112,9 @@ struct pairdiag {
     int omega = 0, n = 0;
     pairdiag_options opt{};
     std::vector<double> e, G, d;
-    int64_t dim = 0, nnz = 0;
+    int64_t dim = 0, nnz = 0;        // of the space the solver works in (kept states when truncated)
+    int64_t full_dim = 0, full_nnz = 0;   // C(Omega, N) and its off-diagonal nonzeros
+    int32_t *d_kmap = nullptr;       // truncated space (Sec. 3.5): full index -> kept index, -1 dropped
     Blocks B{};
     int device = 0;
     cudaStream_t st = nullptr;
@@ -165,7 +167,7 @@ void free_all(pairdiag *h)
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64,
-                    h->d_L64, h->d_L32, h->d_lockc};
+                    h->d_L64, h->d_L32, h->d_lockc, h->d_kmap};
     // the blocks go back to the library's cache: no queued kernel may still use
     // them (cudaFree gave the same guarantee by synchronising the device)
     cudaDeviceSynchronize();
@@ -228,8 +230,8 @@ int build_tables(pairdiag *h)
         if (base[b] != run) return fail(PD_ECUDA, "internal: block index mismatch at block %zu", b);
         run += host_binom(L, N - __builtin_popcountll(hw[b]));
     }
-    if ((int64_t)run != h->dim) return fail(PD_ECUDA, "internal: blocks cover %llu of %lld states",
-                                            (unsigned long long)run, (long long)h->dim);
+    if ((int64_t)run != h->full_dim) return fail(PD_ECUDA, "internal: blocks cover %llu of %lld states",
+                                                 (unsigned long long)run, (long long)h->full_dim);
     // low-word tables
     const int nL = 1 << L;
     std::vector<uint16_t> lowword(nL), rankL(nL);
@@ -479,6 +481,12 @@ int init_start(pairdiag *h, int dtype)
         if (h->opt.start == PD_START_HF) {
             double dmin, dmax;
             PD_TRY(pairdiag_monopole(h, &dmin, &dmax, &pos));
+            if (h->d_kmap) {                      // its kept index (the lowest state is always kept)
+                int32_t m = -1;
+                PD_CUDA(cudaMemcpy(&m, h->d_kmap + pos, sizeof m, cudaMemcpyDeviceToHost));
+                if (m < 0) return fail(PD_ECUDA, "internal: the lowest state was dropped");
+                pos = m;
+            }
         }
         const size_t es = dtype == 0 ? 8 : 4;
         PD_CUDA(cudaMemsetAsync(q0, 0, es * (size_t)dim, h->st));
@@ -694,6 +702,8 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     for (int p = 0; p < omega; ++p) h->d[p] = 2.0 * e[p] + G[p * omega + p];
     h->dim = (int64_t)host_binom(omega, n_pairs);
     h->nnz = h->dim * (int64_t)n_pairs * (int64_t)(omega - n_pairs);
+    h->full_dim = h->dim;
+    h->full_nnz = h->nnz;
     int st = PD_OK;
     do {
         if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); st = fail(PD_ECUDA, "no CUDA device"); break; }
@@ -775,7 +785,8 @@ int64_t pairdiag_nnz(const pairdiag_t *h) { return h ? h->nnz : -1; }
 int pairdiag_basis_dev(const pairdiag_t *h, int64_t first, int64_t count, uint64_t *out_dev)
 {
     if (!h || (!out_dev && count > 0)) return fail(PD_EINVAL, "null argument");
-    if (first < 0 || count < 0 || first + count > h->dim) return fail(PD_EINVAL, "range outside [0, dim)");
+    if (first < 0 || count < 0 || first + count > h->full_dim)
+        return fail(PD_EINVAL, "range outside [0, C(omega, n_pairs))");
     PD_CUDA(basis_launch(h->omega, h->n, h->d_binom, first, count, out_dev, h->st));
     return PD_OK;
 }
@@ -784,10 +795,10 @@ int pairdiag_basis(const pairdiag_t *h, uint64_t *out)
 {
     if (!h || !out) return fail(PD_EINVAL, "null argument");
     uint64_t *d = nullptr;
-    PD_TRY(dalloc(&d, (size_t)h->dim));
-    int st = pairdiag_basis_dev(h, 0, h->dim, d);
+    PD_TRY(dalloc(&d, (size_t)h->full_dim));
+    int st = pairdiag_basis_dev(h, 0, h->full_dim, d);
     if (st == PD_OK) {
-        cudaError_t e1 = cudaMemcpyAsync(out, d, sizeof(uint64_t) * h->dim, cudaMemcpyDeviceToHost, h->st);
+        cudaError_t e1 = cudaMemcpyAsync(out, d, sizeof(uint64_t) * h->full_dim, cudaMemcpyDeviceToHost, h->st);
         cudaError_t e2 = cudaStreamSynchronize(h->st);
         if (e1 != cudaSuccess || e2 != cudaSuccess) st = fail(PD_ECUDA, "basis copy failed");
     }
@@ -854,6 +865,7 @@ int pairdiag_set_start_weights(pairdiag_t *h, const double *w)
 int pairdiag_product_fit(pairdiag_t *h, const double *v_dev, double *w)
 {
     if (!h || !v_dev || !w) return fail(PD_EINVAL, "null argument");
+    if (h->d_kmap) return fail(PD_ENOTSUP, "product fit of a truncated space");
     return product_fit(h->B, v_dev, w, h->st);
 }
 
@@ -954,6 +966,187 @@ int pairdiag_lowest_states_dev(pairdiag_t *h, int k, double tol, double *energie
     if (status == PD_ENOCONV) return fail(PD_ENOCONV, "a state missed tol %.3g", tol);
     return PD_OK;
 }
+
+// ---- truncated model space (Sec. 3.5) ---------------------------------------------
+namespace {
+
+constexpr int kHistBuckets = 8192;   // buckets per histogram pass
+constexpr int64_t kMaxBins = (int64_t)1 << 40;
+
+// back to the full space: drop the map and every vector sized by the old space
+void drop_space(pairdiag *h)
+{
+    cudaStreamSynchronize(h->st);
+    void **vecs[] = {&h->d_Q[0], &h->d_Q[1], &h->d_p[0], &h->d_p[1], (void **)&h->d_v64, (void **)&h->d_w64,
+                     (void **)&h->d_L64, (void **)&h->d_L32, (void **)&h->d_kmap};
+    for (void **v : vecs) {
+        pool_free(*v);
+        *v = nullptr;
+    }
+    h->Qwin[0] = h->Qwin[1] = 0;
+    h->lock_cap = 0;
+    h->n_locked = 0;
+    h->start.clear();
+    h->B.kept_map = nullptr;
+    h->dim = h->full_dim;
+    h->nnz = h->full_nnz;
+    h->ldq = (h->dim + 3) / 4 * 4;
+    h->hxgrid[0] = hx_grid(h->B, 0);
+    h->hxgrid[1] = hx_grid(h->B, 1);
+}
+
+// The kept states of Sec. 3.5 and the map full index -> kept index.  Returns
+// the kept count in *kept (== full_dim when nothing is dropped, no map made).
+int build_truncation(pairdiag *h, int64_t limit, int64_t bins, int64_t *kept)
+{
+    const int64_t full = h->full_dim;
+    *kept = full;
+    if (limit >= full) return PD_OK;                 // no truncation
+    double lo, hi;
+    int64_t pos;
+    PD_TRY(pairdiag_monopole(h, &lo, &hi, &pos));
+    if (!(hi > lo)) return PD_OK;                     // every diagonal element equal
+    const Blocks &B = h->B;
+    const int grid = h->rgrid;
+    cudaStream_t st = h->st;
+    std::vector<void *> tmp;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        for (void *p : tmp) pool_free(p);
+    };
+    auto talloc = [&](void **p, size_t bytes) -> int {
+        const cudaError_t e = pool_alloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PD_ENOMEM, "truncation: %zu bytes: %s", bytes, cudaGetErrorString(e));
+        }
+        tmp.push_back(*p);
+        return PD_OK;
+    };
+    int rc = [&]() -> int {
+        // the cutoff bin: the lowest bin at which the running count reaches the
+        // limit, found by histograms over ever narrower bin ranges
+        unsigned long long *hist = nullptr;
+        PD_TRY(talloc((void **)&hist, sizeof(unsigned long long) * kHistBuckets));
+        std::vector<unsigned long long> hh(kHistBuckets);
+        int64_t lo_bin = 0, span = bins;
+        unsigned long long below = 0;                 // states in bins below lo_bin
+        const unsigned long long need = (unsigned long long)limit;
+        int64_t cut = -1;
+        for (int level = 0; level < 8 && cut < 0; ++level) {
+            int shift = 0;
+            while (((span + ((int64_t)1 << shift) - 1) >> shift) > kHistBuckets) ++shift;
+            const int nb = (int)((span + ((int64_t)1 << shift) - 1) >> shift);
+            PD_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nb, st));
+            PD_CUDA(trunc_hist_launch(B, h->d_d64, lo, hi, bins, lo_bin, shift, nb, hist, grid, st));
+            PD_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, st));
+            PD_CUDA(cudaStreamSynchronize(st));
+            int j = 0;
+            unsigned long long run = below;
+            while (j < nb && run + hh[j] < need) run += hh[j++];
+            if (j == nb) return fail(PD_ECUDA, "internal: truncation histogram holds %llu of %lld states",
+                                     run, (long long)limit);
+            below = run;
+            lo_bin += (int64_t)j << shift;
+            if (shift == 0) cut = lo_bin;
+            else span = std::min<int64_t>((int64_t)1 << shift, bins - lo_bin);
+        }
+        if (cut < 0) return fail(PD_ECUDA, "internal: truncation cutoff not found");
+        // kept states per block, their first kept index, and the map
+        int *blk_kept = nullptr;
+        PD_TRY(talloc((void **)&blk_kept, sizeof(int) * (size_t)B.nblocks));
+        PD_CUDA(trunc_count_launch(B, h->d_d64, lo, hi, bins, cut, blk_kept, grid, st));
+        std::vector<int> cnt((size_t)B.nblocks);
+        PD_CUDA(cudaMemcpyAsync(cnt.data(), blk_kept, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaStreamSynchronize(st));
+        std::vector<int64_t> first(cnt.size());
+        int64_t total = 0;
+        for (size_t b = 0; b < cnt.size(); ++b) {
+            first[b] = total;
+            total += cnt[b];
+        }
+        if (total < limit || total > full) return fail(PD_ECUDA, "internal: %lld states kept", (long long)total);
+        *kept = total;
+        if (total == full) return PD_OK;              // the cutoff bin is the last one
+        if (total > (int64_t)INT32_MAX) return fail(PD_ENOTSUP, "more than 2^31 - 1 kept states");
+        int64_t *d_first = nullptr;
+        PD_TRY(talloc((void **)&d_first, sizeof(int64_t) * first.size()));
+        PD_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice, st));
+        PD_TRY(dalloc(&h->d_kmap, (size_t)full));
+        PD_CUDA(trunc_map_launch(B, h->d_d64, lo, hi, bins, cut, d_first, h->d_kmap, grid, st));
+        PD_CUDA(cudaStreamSynchronize(st));
+        return PD_OK;
+    }();
+    cleanup();
+    return rc;
+}
+
+}  // namespace
+
+int pairdiag_truncate(pairdiag_t *h, int64_t dimension_limit, int64_t bins, int64_t *kept_dim)
+{
+    if (!h || !kept_dim) return fail(PD_EINVAL, "null argument");
+    if (dimension_limit < 0) return fail(PD_EINVAL, "dimension_limit < 0");
+    if (bins == 0) bins = 100000000;
+    if (bins < 1 || bins > kMaxBins) return fail(PD_EINVAL, "bins outside 1..2^40");
+    PD_CUDA(cudaSetDevice(h->device));
+    drop_space(h);
+    *kept_dim = h->dim;
+    if (dimension_limit == 0) return PD_OK;
+    int64_t kept = 0;
+    int rc = build_truncation(h, dimension_limit, bins, &kept);
+    if (rc == PD_OK && h->d_kmap) {
+        h->dim = kept;
+        h->ldq = (kept + 3) / 4 * 4;
+        h->B.kept_map = h->d_kmap;
+        h->hxgrid[0] = hx_grid(h->B, 0);
+        h->hxgrid[1] = hx_grid(h->B, 1);
+        // off-diagonal nonzeros of the truncated matrix: H x with every G_ij = 1
+        // and d = 0 on x = 1 counts each row's kept targets (exact in FP64)
+        rc = [&]() -> int {
+            std::vector<double> ones((size_t)h->omega * h->omega, 1.0), zeros(h->omega, 0.0);
+            double *g1 = nullptr, *d0 = nullptr;
+            PD_TRY(upload(&g1, ones));
+            const int r0 = upload(&d0, zeros);
+            if (r0 != PD_OK) { pool_free(g1); return r0; }
+            int r = ensure_fp64_pair(h);
+            if (r == PD_OK) r = product_start(h->B, zeros.data(), 0, h->d_v64, h->st);   // kept entries = 1
+            if (r == PD_OK) {
+                const HxProblem P1{g1, d0, nullptr, nullptr};
+                cudaError_t ce = hx_launch(h->B, P1, 0, h->d_v64, h->d_w64, h->d_tk, h->hxgrid[0], h->st);
+                if (ce == cudaSuccess)
+                    ce = multidot_launch(0, h->d_w64, kept, 1, h->d_v64, kept, h->d_part, &h->d_S->dots[0], h->st,
+                                         nullptr, &h->d_tk->vec_done);
+                double c = 0.0;
+                if (ce == cudaSuccess) ce = cudaMemcpyAsync(&c, &h->d_S->dots[0], sizeof c, cudaMemcpyDeviceToHost, h->st);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+                if (ce != cudaSuccess) r = fail(PD_ECUDA, "truncation nonzero count: %s", cudaGetErrorString(ce));
+                else h->nnz = (int64_t)std::llround(c);
+            }
+            cudaStreamSynchronize(h->st);
+            pool_free(g1);
+            pool_free(d0);
+            return r;
+        }();
+    }
+    if (rc != PD_OK) {
+        drop_space(h);
+        return rc;
+    }
+    *kept_dim = h->dim;
+    return PD_OK;
+}
+
+int pairdiag_kept_map_dev(const pairdiag_t *h, int32_t *map_dev)
+{
+    if (!h || !map_dev) return fail(PD_EINVAL, "null argument");
+    if (!h->d_kmap) return fail(PD_EINVAL, "the handle holds the full space (no truncation active)");
+    PD_CUDA(cudaMemcpyAsync(map_dev, h->d_kmap, sizeof(int32_t) * (size_t)h->full_dim, cudaMemcpyDeviceToDevice,
+                            h->st));
+    return PD_OK;
+}
+
+int64_t pairdiag_full_dim(const pairdiag_t *h) { return h ? h->full_dim : -1; }
 
 int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, int m, const void *p_dev,
                       int64_t n, double *out)

@@ -79,6 +79,15 @@ __device__ __forceinline__ uint64_t block_base(uint64_t h, int L, int N,
     return s;
 }
 
+// x at full index i of a truncated space: the kept state's element, 0 for a
+// dropped state (a hop to it contributes nothing: the principal submatrix)
+template <typename T>
+__device__ __forceinline__ T x_kept(const T *__restrict__ x, const int32_t *__restrict__ map, uint64_t i)
+{
+    const int32_t m = __ldg(map + i);
+    return m >= 0 ? __ldg(x + m) : T(0);
+}
+
 // x^T y over this warp's rows of one basis block (y as stored) into sw[warp]
 // (lane 0).  No barrier: thread 0 adds the warp sums in warp order after the
 // barrier that opens the next block (block_sum_deferred).
@@ -125,14 +134,15 @@ __device__ __forceinline__ void hx_finish(Tickets *tk, int64_t nblocks, const do
 // the problem's own vector; sG/sd/sRank hold its G, d and rank table.  Called
 // by every thread of the CTA (it contains barriers).  swdot (nullable): the
 // block's x^T y per warp (warp_dot).
-template <typename T, typename A, int R>
+template <typename T, typename A, int R, bool TR = false>
 __device__ __forceinline__ void hx_block(const int omega, const int L, const int H, const int N,
                                          const uint64_t h, const uint64_t base,
                                          const uint16_t *__restrict__ lowword,
                                          const uint64_t *__restrict__ binom,
                                          const A *sG, const A *sd, const uint16_t *sRank, T *sx, T *sxn,
                                          HHop<A> *sHH, uint64_t *sMX, const T *__restrict__ x,
-                                         T *__restrict__ y, double *swdot)
+                                         T *__restrict__ y, double *swdot,
+                                         const int32_t *__restrict__ map = nullptr)
 {
     const int tid = threadIdx.x;
     const uint32_t maskL = (1u << L) - 1u;
@@ -160,7 +170,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         const bool ok = occ ? (k + 1 <= L) : (k >= 1);
         sMX[t] = ok ? block_base(h ^ bit, L, N, binom) : ~0ull;
     }
-    for (int r = tid; r < nk; r += kThreads) sx[r] = x[base + r];
+    for (int r = tid; r < nk; r += kThreads) sx[r] = TR ? x_kept(x, map, base + r) : x[base + r];
     __syncthreads();
 
     A Dh = A(0);
@@ -213,7 +223,11 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = tid + i * kThreads;
-            if (r < nk) acc[i] += g * A(__ldg(xb + r));
+            if constexpr (TR) {
+                if (r < nk) acc[i] += g * A(x_kept(x, map, sHH[j].base + r));
+            } else {
+                if (r < nk) acc[i] += g * A(__ldg(xb + r));
+            }
         }
     }
 
@@ -225,7 +239,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         const bool occ_t = (h >> t) & 1ull;
         const int n2 = (int)__ldg(binom + L * kBinomStride + (occ_t ? k + 1 : k - 1));
         __syncthreads();
-        for (int r = tid; r < n2; r += kThreads) sxn[r] = x[b2 + r];
+        for (int r = tid; r < n2; r += kThreads) sxn[r] = TR ? x_kept(x, map, b2 + r) : x[b2 + r];
         __syncthreads();
         const int go = L + t;
         if (occ_t) {                           // pair: high orbit go -> empty low orbit q
@@ -264,12 +278,20 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int r = tid + i * kThreads;
-        if (r < nk) y[base + r] = T(acc[i]);
+        if constexpr (TR) {
+            if (r < nk) {                     // dropped rows are not part of y
+                const int32_t m = __ldg(map + base + r);
+                if (m >= 0) y[m] = T(acc[i]);
+            }
+        } else {
+            if (r < nk) y[base + r] = T(acc[i]);
+        }
     }
+    // (truncated: a dropped row has sx = 0, so it adds nothing to the dot)
     if (swdot) warp_dot<T, A, R>(acc, sx, nk, swdot);
 }
 
-template <typename T, typename A, int R>
+template <typename T, typename A, int R, bool TR>
 __global__ void __launch_bounds__(kThreads)
 hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
           const T *__restrict__ x, T *__restrict__ y, Tickets *tk, const int *__restrict__ skip,
@@ -308,8 +330,8 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
         }
         if (b >= B.nblocks) break;
 
-        hx_block<T, A, R>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
-                          sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? swdot : nullptr);
+        hx_block<T, A, R, TR>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
+                              sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? swdot : nullptr, B.kept_map);
         prev = b;
     }
     hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
@@ -716,14 +738,15 @@ constexpr size_t kSmemLimit = 200 * 1024;
 template <typename T, typename A>
 bool use_v2(const Blocks &B)
 {
-    if (B.variant != 2) return false;
+    if (B.variant != 2 || B.kept_map) return false;     // a truncated space runs variant 1
     return layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total <= kSmemLimit;
 }
 
 template <typename T, typename A, int R>
 const void *kernel_fn(const Blocks &B)
 {
-    return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R>;
+    if (B.kept_map) return (const void *)hx_kernel<T, A, R, true>;
+    return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R, false>;
 }
 
 template <typename T, typename A>
@@ -744,12 +767,15 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     if (err != cudaSuccess) return err;
     double *bp = dot ? dot->blk_part : nullptr;
     double *out = dot ? dot->out : nullptr;
-    if (v2)
+    if (B.kept_map)
+        hx_kernel<T, A, R, true><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                               static_cast<T *>(y), tk, skip, bp, out);
+    else if (v2)
         hx2_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                           static_cast<T *>(y), tk, skip, bp, out);
     else
-        hx_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                         static_cast<T *>(y), tk, skip, bp, out);
+        hx_kernel<T, A, R, false><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                                static_cast<T *>(y), tk, skip, bp, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -843,6 +869,95 @@ __global__ void monopole_final(const double *__restrict__ part, int n, double *_
     out[0] = vmin; out[1] = vmax; out[2] = __longlong_as_double(imin);
 }
 
+// ---- truncated model space (Sec. 3.5) ------------------------------------------
+// Diagonal element of row r of a block (ascending orbit order, as the oracle
+// and the monopole kernel sum it) and its histogram bin, both in FP64.
+__device__ __forceinline__ long long trunc_bin(const Blocks &B, const double *__restrict__ d, uint64_t h,
+                                               uint32_t l, double lo, double hi, long long bins)
+{
+    double D = 0.0;
+    for (uint32_t w = l; w; w &= w - 1) D += d[__ffs(w) - 1];
+    for (uint64_t w = h; w; w &= w - 1) D += d[B.L + __ffsll((long long)w) - 1];
+    const long long b = (long long)floor((D - lo) / (hi - lo) * (double)bins);
+    return b < bins - 1 ? b : bins - 1;
+}
+
+constexpr int kTruncMaxBuckets = 8192;
+
+__global__ void __launch_bounds__(kThreads)
+trunc_hist_kernel(const Blocks B, const double *__restrict__ d, double lo, double hi, long long bins,
+                  long long lo_bin, int shift, int nbuckets, unsigned long long *__restrict__ hist)
+{
+    __shared__ unsigned int sh[kTruncMaxBuckets];
+    for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const long long span = (long long)nbuckets << shift;
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            const long long bin = trunc_bin(B, d, h, lw[r], lo, hi, bins) - lo_bin;
+            if (bin >= 0 && bin < span) atomicAdd(&sh[bin >> shift], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbuckets; i += blockDim.x)
+        if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+trunc_count_kernel(const Blocks B, const double *__restrict__ d, double lo, double hi, long long bins,
+                   long long cut, int *__restrict__ blk_kept)
+{
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        int cnt = 0;
+        for (int r0 = 0; r0 < nk; r0 += kThreads) {
+            const int r = r0 + (int)threadIdx.x;
+            cnt += __syncthreads_count(r < nk && trunc_bin(B, d, h, lw[r < nk ? r : 0], lo, hi, bins) <= cut);
+        }
+        if (threadIdx.x == 0) blk_kept[b] = cnt;
+    }
+}
+
+// kept index = first kept index of the block + rank among the block's kept rows
+__global__ void __launch_bounds__(kThreads)
+trunc_map_kernel(const Blocks B, const double *__restrict__ d, double lo, double hi, long long bins,
+                 long long cut, const int64_t *__restrict__ blk_first, int32_t *__restrict__ map)
+{
+    __shared__ int swarp[kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        const uint16_t *lw = B.lowword + B.lo_off[k];
+        const int64_t first = blk_first[b];
+        int running = 0;
+        for (int r0 = 0; r0 < nk; r0 += kThreads) {
+            const int r = r0 + (int)threadIdx.x;
+            const bool keep = r < nk && trunc_bin(B, d, h, lw[r < nk ? r : 0], lo, hi, bins) <= cut;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int before = __popc(bal & ((1u << lane) - 1u));
+            if (lane == 0) swarp[w] = __popc(bal);
+            __syncthreads();
+            int woff = 0, total = 0;
+            for (int i = 0; i < kThreads / 32; ++i) {
+                woff += i < w ? swarp[i] : 0;
+                total += swarp[i];
+            }
+            if (r < nk) map[base + r] = keep ? (int32_t)(first + running + woff + before) : -1;
+            running += total;
+            __syncthreads();
+        }
+    }
+}
+
 // ---- occupation numbers 2 <v| S+_p S-_p |v> ------------------------------------
 __global__ void __launch_bounds__(kThreads)
 occ_kernel(const Blocks B, const double *__restrict__ v, double *__restrict__ part)
@@ -858,7 +973,14 @@ occ_kernel(const Blocks B, const double *__restrict__ v, double *__restrict__ pa
         const uint16_t *lw = B.lowword + B.lo_off[k];
         double mine = 0.0;
         for (int r = threadIdx.x; r < nk; r += blockDim.x) {
-            const double w = v[base + r] * v[base + r];
+            double vr;
+            if (B.kept_map) {                     // truncated space: dropped states hold nothing
+                const int32_t m = B.kept_map[base + r];
+                vr = m >= 0 ? v[m] : 0.0;
+            } else {
+                vr = v[base + r];
+            }
+            const double w = vr * vr;
             mine += w;
             for (uint32_t m = lw[r]; m; m &= m - 1) atomicAdd(&acc[__ffs(m) - 1], w);
         }
@@ -978,6 +1100,32 @@ cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials
     monopole_kernel<<<grid, kThreads, 0, st>>>(B, d64, partials);
     monopole_final<<<1, 32, 0, st>>>(partials, grid, out);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t trunc_hist_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                              int64_t lo_bin, int shift, int nbuckets, unsigned long long *hist, int grid,
+                              cudaStream_t st)
+{
+    if (nbuckets < 1 || nbuckets > kTruncMaxBuckets) return cudaErrorInvalidValue;
+    trunc_hist_kernel<<<grid, kThreads, 0, st>>>(B, d64, lo, hi, bins, lo_bin, shift, nbuckets, hist);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t trunc_count_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                               int64_t cut, int *blk_kept, int grid, cudaStream_t st)
+{
+    trunc_count_kernel<<<grid, kThreads, 0, st>>>(B, d64, lo, hi, bins, cut, blk_kept);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t trunc_map_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                             int64_t cut, const int64_t *blk_first, int32_t *map, int grid, cudaStream_t st)
+{
+    trunc_map_kernel<<<grid, kThreads, 0, st>>>(B, d64, lo, hi, bins, cut, blk_first, map);
+    count_launches(1);
     return cudaGetLastError();
 }
 

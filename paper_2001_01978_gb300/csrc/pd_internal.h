@@ -84,6 +84,10 @@ struct Blocks {
     const uint64_t *binom;           // [64*64]
     int lo_off[kMaxLow + 2];         // group offsets into lowword
     int variant;                     // H*x kernel: 0 automatic, 1 staged per neighbour, 2 all staged
+    // truncated model space (Sec. 3.5): kept_map[full index] = position among the
+    // kept states, -1 for a dropped state; nullptr = the full space.  Vectors of
+    // a truncated handle hold the kept states only, in basis order.
+    const int32_t *kept_map;
 };
 
 // ---- many problems at once (batched solver) ---------------------------------
@@ -292,6 +296,20 @@ cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const 
                       Tickets *tk, int grid, cudaStream_t st, const int *skip = nullptr,
                       const HxDot *dot = nullptr);
 int hx_grid(const Blocks &B, int precision);
+// Truncation (Sec. 3.5).  The bin of a state is floor((D - lo) / (hi - lo) * bins)
+// in FP64, clamped to bins - 1, with D its diagonal element summed in ascending
+// orbit order; lo/hi the extreme diagonal elements.
+// hist (device, zeroed by the caller): counts of the bins b with
+// lo_bin <= b < lo_bin + (nbuckets << shift), per bucket (b - lo_bin) >> shift
+cudaError_t trunc_hist_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                              int64_t lo_bin, int shift, int nbuckets, unsigned long long *hist, int grid,
+                              cudaStream_t st);
+// blk_kept[b] = kept states of block b (bin <= cut)
+cudaError_t trunc_count_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                               int64_t cut, int *blk_kept, int grid, cudaStream_t st);
+// map[i] = blk_first[b] + rank among the kept states of its block, -1 if dropped
+cudaError_t trunc_map_launch(const Blocks &B, const double *d64, double lo, double hi, int64_t bins,
+                             int64_t cut, const int64_t *blk_first, int32_t *map, int grid, cudaStream_t st);
 // Monopole_Min/Max/Posit_Min: partials[grid*3] scratch; out[0]=min, out[1]=max, out[2]=pos (as double bits)
 cudaError_t monopole_launch(const Blocks &B, const double *d64, double *partials, int grid,
                             double *out, cudaStream_t st);

@@ -356,7 +356,12 @@ product_start_kernel(const Blocks B, const double *__restrict__ w, double shift,
         for (int r = threadIdx.x; r < nk; r += blockDim.x) {
             double s = sh;
             for (uint32_t m = lw[r]; m; m &= m - 1) s += sw[__ffs(m) - 1];
-            v[base + r] = (T)exp(s);
+            if (B.kept_map) {                   // truncated space: kept states only
+                const int32_t m = B.kept_map[base + r];
+                if (m >= 0) v[m] = (T)exp(s);
+            } else {
+                v[base + r] = (T)exp(s);
+            }
         }
     }
 }

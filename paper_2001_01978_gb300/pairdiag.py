@@ -76,6 +76,9 @@ _SIGNATURES = {
     "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_lowest_states_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, _P, _P,
                                                   ctypes.POINTER(pairdiag_info)]),
+    "pairdiag_truncate": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "pairdiag_kept_map_dev": (ctypes.c_int, [_H, _P]),
+    "pairdiag_full_dim": (ctypes.c_int64, [_H]),
     "pairdiag_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "pairdiag_multidot": (ctypes.c_int, [_H, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "pairdiag_tridiag_lowest": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, _P, _P]),
@@ -196,8 +199,28 @@ def pairdiag_nnz(h) -> int:
     return int(lib().pairdiag_nnz(h))
 
 
+def pairdiag_full_dim(h) -> int:
+    return int(lib().pairdiag_full_dim(h))
+
+
+def pairdiag_truncate(h, dimension_limit: int, bins: int = 0) -> int:
+    """Truncated model space of Sec. 3.5 (0 restores the full space); returns the
+    new dimension (the kept states)."""
+    kept = ctypes.c_int64()
+    _check(lib().pairdiag_truncate(h, dimension_limit, bins, ctypes.byref(kept)))
+    return kept.value
+
+
+def pairdiag_kept_map_dev(h, out) -> None:
+    """Kept index of every full-space state (-1 dropped) into an int32 device tensor."""
+    import torch
+    if out.numel() < pairdiag_full_dim(h):
+        raise ValueError("out must hold C(omega, n_pairs) elements")
+    _check(lib().pairdiag_kept_map_dev(h, _dev_ptr(out, torch.int32)))
+
+
 def pairdiag_basis(h) -> np.ndarray:
-    out = np.empty(pairdiag_dim(h), dtype=np.uint64)
+    out = np.empty(pairdiag_full_dim(h), dtype=np.uint64)
     _check(lib().pairdiag_basis(h, _np_ptr(out)))
     return out
 

@@ -79,7 +79,7 @@ def _random_states(omega, n, count, seed):
     return words
 
 
-@pytest.mark.parametrize("omega,n", [(12, 6), (20, 9), (24, 12), (32, 16), (38, 10), (50, 5), (62, 31), (62, 1)])
+@pytest.mark.parametrize("omega,n", [(12, 6), (20, 9), (24, 12), (32, 16), (38, 10), (44, 7), (50, 5), (62, 3), (62, 1)])
 def test_rank_vs_oracle_hash(omega, n):
     """pairdiag_rank_dev on random states equals the oracle's hash f - 1 (Sec. 3.2),
     bit for bit, including the first and last states of the basis."""
