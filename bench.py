@@ -664,6 +664,14 @@ def run_batch(args):
     forms = [("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM), ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)]
     if ws is not None:
         forms.insert(0, ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP))
+    # the oracle's E0 of twelve stratified problems (tests/golden/make_golden.py)
+    picks_ref = {}
+    gf = ROOT / "tests" / "golden" / f"batch{len(probs)}_s5_picks_e0.txt"
+    if gf.exists():
+        for line in gf.read_text().splitlines():
+            if line.strip() and not line.startswith("#"):
+                row = line.split()
+                picks_ref[int(row[0])] = float(row[4])
     out = {}
     for name, prec, start in forms:
         opt = pd.pairdiag_default_options(precision=prec, window=args.window, start=start)
@@ -682,11 +690,13 @@ def run_batch(args):
         ms = statistics.median(times)
         lat = res["latency_ms"]
         iters = res["iterations"]
+        errs = [abs(res["e0"][i] - ref) / abs(ref) for i, ref in picks_ref.items()]
         out[name] = {"batch_ms": ms, "solves_per_s": len(probs) / (ms * 1e-3),
                      "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
                      "converged_frac": float(np.mean(res["converged"])),
                      "iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
-                     "e0_first": float(res["e0"][0])}
+                     "e0_max_rel_err_vs_oracle": max(errs) if errs else None,
+                     "oracle_picks": len(errs)}
     e_m = np.array([0.0])
     print(json.dumps({"batch": True, "workload": "mean-field batch: %d problems, Omega ~ U{10..22}, seed 5" % len(probs),
                       "total_dim": int(sum(dims)), "nnz_offdiag_per_batched_hx": int(nnz), "tol": args.tol,

@@ -79,7 +79,10 @@ typedef struct {
                                refinement (PD_PREC_MIXED only); default 5e-6 */
     int      hx_variant;    /* H*x kernel: 0 = automatic (default, currently 1), 1 = neighbour
                                blocks staged one at a time, 2 = all neighbour blocks staged at
-                               once (falls back to 1 when its shared memory does not fit) */
+                               once, 3 = no staging, every target gathered from global memory
+                               (for small blocks, far from half filling); 2 and 3 fall back
+                               to 1 when their shared memory does not fit.  A truncated
+                               handle (pairdiag_truncate) runs variant 1 */
 } pairdiag_options;
 
 typedef struct {
@@ -302,16 +305,25 @@ typedef struct {
     int    stalled;         /* mixed form: FP32 cycles stopped at their rounding floor */
     double rel_residual;    /* relative residual of the returned energy's vector: FP64
                                ||Hv - Ev||/|E| after refinement (mixed), else |beta_1/alpha_1| */
-    double latency_ms;      /* device time from the start of the cycles to the end of the
-                               cycle in which this problem finished */
+    double latency_ms;      /* device clock from the start of the call's device work to the
+                               moment this problem's returned energy was final (after the
+                               FP64 refinement in the mixed form) */
 } pairdiag_batch_result;
 
 /*
- * Ground states of `count` independent pairing Hamiltonians (Eq. 2) in one
- * lock-step restarted-Lanczos run: the mean-field use case of Sec. 1/6, where a
- * pairing solve sits inside every self-consistent iteration.  Every kernel
- * serves all problems in one launch; converged problems drop out; each restart
- * cycle is replayed from a captured CUDA graph.
+ * Ground states of `count` independent pairing Hamiltonians (Eq. 2): the
+ * mean-field use case of Sec. 1/6, where a pairing solve sits inside every
+ * self-consistent iteration.  The problems are sorted by dimension and split
+ * into up to four size classes (the smallest 50 %, then 30 %, 15 % and 5 %;
+ * one class below 64 problems), each on its own stream, the smaller ones at a
+ * higher stream priority, so that small problems are not held back by the
+ * largest.  Within a class the problems run restarted Lanczos in lock step:
+ * every kernel serves all of them in one launch and converged problems drop
+ * out.  The restart cycles of a class are one CUDA graph whose conditional
+ * WHILE node repeats the cycle until a device-side test finds no problem
+ * running (or max_restarts is reached): the host does not synchronise between
+ * cycles.  The mixed form synchronises once per class after the FP64
+ * refinement, to start FP64 cycles for problems that need them.
  *   omega, n_pairs : host [count]
  *   e_all          : host, the e vectors of all problems concatenated (sum of omega)
  *   G_all          : host, the row-major G matrices concatenated (sum of omega^2);
@@ -344,8 +356,12 @@ int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs,
  * with b blocked is the seniority-zero space of n_pairs pairs on the other
  * omega-1 orbits, and
  *     E_b = e_b + E0(Eq. 2 with e and G restricted to the orbits i != b).
- * Each subspace is solved as a handle of this library on the restricted
- * (e, G), in turn, on the current CUDA device.
+ * With block = -1 and a PD_START_RANDOM or PD_START_MLP start, all omega
+ * subspaces (of equal size) are solved together by the batched solver
+ * (pairdiag_batch_ground_state) and, when vec or occ is wanted, the winning
+ * subspace once more as a handle for its vector and occupations (e0 and
+ * energies stay those of the batched solve; info describes the second solve).  Otherwise each subspace is a handle of this library on the
+ * restricted (e, G), solved in turn.  Everything runs on the current device.
  *   omega, n_pairs : omega in 2..62, n_pairs in 0..omega-1 (2*n_pairs+1 particles)
  *   e, G           : host, as in pairdiag_create (G exactly symmetric)
  *   block          : -1 = every b, the lowest E_b is returned (the paper's Block = 0);
@@ -376,7 +392,7 @@ int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e, const dou
 /*
  * H*x schedule autotuner (an addition of this library; the paper has a single
  * CPU code path).  For one problem and precision it times the H*x kernel for
- * every block split L = low_bits in [min(omega,8), min(omega,13)] and both
+ * every block split L = low_bits in [min(omega,8), min(omega,13)] and the three
  * kernel variants (median of `reps` launches on a random vector, CUDA events)
  * and records the fastest (low_bits, hx_variant) for (omega, n_pairs,
  * precision) in a process-wide table.  pairdiag_create and the batched solver

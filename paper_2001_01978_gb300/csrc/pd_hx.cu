@@ -345,7 +345,7 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 template <typename T, typename A, int R>
 __global__ void __launch_bounds__(kThreads)
 hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__restrict__ dall,
-                const T *__restrict__ x, T *__restrict__ y, unsigned long long *__restrict__ counter,
+                const T *__restrict__ x, T *__restrict__ y, unsigned long long *counter,
                 const int *__restrict__ skip, int skip_stride)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -385,6 +385,9 @@ hx_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__res
                           BB.lowword_all + dsc.tab_off, BB.binom, sG, sd, sRank, sx, sxn, sHH, sMX,
                           x + dsc.vec_off, y + dsc.vec_off, nullptr);
     }
+    // the last CTA to finish returns the block counter to zero (arrive_last
+    // resets its own ticket), so the next launch needs no memset
+    if (arrive_last(counter + 1) && tid == 0) counter[0] = 0ull;
 }
 
 // ---- variant 2: every neighbouring block of the high<->low hops staged at once --
@@ -730,6 +733,318 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
 
+// ---- variant 3: no staging rounds; hop tables in O(1) per entry ------------------
+// Variants 1 and 2 stage neighbour blocks in shared memory, which pays when
+// blocks are large (half filling).  Far from half filling most blocks hold a
+// few rows (C(12,0..1) = 1..12 at Omega=38, N=10), and there variant 1's H
+// staging rounds (each a memory latency plus two barriers) and the per-entry
+// block_base loops of the hop tables dominate.  Variant 3 gathers every
+// target straight from global memory (L2) with one barrier per block, and
+// builds the hop tables from prefix sums of binomials over the block's high
+// pairs.  With P_1 < ... < P_ph the occupied high orbits (ordinals k+1..N),
+//   A_i = C(L+P_i, k+i), B_i = C(L+P_i, k+i-1), C_i = C(L+P_i, k+i+1)
+// and SA, SB, SC their prefix sums (SA[ph] = base(h)):
+//   base(h - P_a + q) = SA[ph] - (SA[b] - SA[a-1]) + (SB[b] - SB[a]) + C(L+q, k+b)   (a <= b)
+//                     = SA[ph] - (SA[a] - SA[b]) + (SC[a-1] - SC[b]) + C(L+q, k+b+1)  (a > b)
+//   base(h - P_a)     = SC[a-1] + SA[ph] - SA[a]              (k+1 low pairs)
+//   base(h + q)       = SB[b] + C(L+q, k+b) + SA[ph] - SA[b]   (k-1 low pairs)
+// with q an empty high orbit and b the number of occupied high orbits below q:
+// the pairs between the moved ones change ordinal by one, the others keep it.
+struct Layout3 {
+    size_t g, d, rank, bin, x, hh, mxo, mxe, sa, sb, sc, pos, emp, eb, total;
+};
+
+template <typename T, typename A>
+__host__ __device__ inline Layout3 layout3(int omega, int L, int H, int N, int max_block, int max_hh)
+{
+    Layout3 s;
+    size_t off = 0;
+    const int h1 = H > 0 ? H : 1;
+    s.g = off;    off = align16(off + sizeof(A) * omega * omega);
+    s.d = off;    off = align16(off + sizeof(A) * omega);
+    s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
+    s.bin = off;  off = align16(off + sizeof(uint64_t) * h1 * (N + 2));
+    s.x = off;    off = align16(off + sizeof(T) * max_block);
+    s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
+    s.mxo = off;  off = align16(off + sizeof(uint64_t) * h1);
+    s.mxe = off;  off = align16(off + sizeof(uint64_t) * h1);
+    s.sa = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
+    s.sb = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
+    s.sc = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
+    s.pos = off;  off = align16(off + sizeof(int) * h1);
+    s.emp = off;  off = align16(off + sizeof(int) * h1);
+    s.eb = off;   off = align16(off + sizeof(int) * h1);
+    s.total = off;
+    return s;
+}
+
+template <typename T, typename A>
+struct Smem3 {
+    A *G, *d;
+    uint16_t *rank;
+    uint64_t *bin, *mxo, *mxe, *sa, *sb, *sc;
+    int *pos, *emp, *eb;
+    T *x;
+    HHop<A> *hh;
+    __device__ Smem3(unsigned char *m, const Layout3 &l)
+        : G(reinterpret_cast<A *>(m + l.g)), d(reinterpret_cast<A *>(m + l.d)),
+          rank(reinterpret_cast<uint16_t *>(m + l.rank)), bin(reinterpret_cast<uint64_t *>(m + l.bin)),
+          mxo(reinterpret_cast<uint64_t *>(m + l.mxo)), mxe(reinterpret_cast<uint64_t *>(m + l.mxe)),
+          sa(reinterpret_cast<uint64_t *>(m + l.sa)), sb(reinterpret_cast<uint64_t *>(m + l.sb)),
+          sc(reinterpret_cast<uint64_t *>(m + l.sc)), pos(reinterpret_cast<int *>(m + l.pos)),
+          emp(reinterpret_cast<int *>(m + l.emp)), eb(reinterpret_cast<int *>(m + l.eb)),
+          x(reinterpret_cast<T *>(m + l.x)), hh(reinterpret_cast<HHop<A> *>(m + l.hh))
+    {
+    }
+};
+
+// One basis block of y = H x in variant 3.  Called by every thread after a
+// barrier that frees the previous block's shared memory; one barrier inside.
+template <typename T, typename A, int R>
+__device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega, const int L, const int H,
+                                          const int N, const uint64_t h, const uint64_t base,
+                                          const uint16_t *__restrict__ lowword, const T *__restrict__ x,
+                                          T *__restrict__ y, double *swdot)
+{
+    const int tid = threadIdx.x;
+    const uint32_t maskL = (1u << L) - 1u;
+    const int ph = __popcll(h);
+    const int k = N - ph;
+    const int nemp = H - ph;
+    const int nhh = ph * nemp;
+    const int NB = N + 2;                         // row stride of s.bin: C(L + p, m), m <= N + 1
+    const int nk = (int)s.bin[k];
+    int lo_off = 0;
+    for (int j = 0; j < k; ++j) lo_off += (int)s.bin[j];
+    const uint16_t *lw = lowword + lo_off;
+
+    for (int r = tid; r < nk; r += kThreads) s.x[r] = x[base + r];
+    if (tid < 32) {                               // warp 0: positions and prefix sums of the high pairs
+        const int lane = tid;
+        const unsigned lt = (1u << lane) - 1u;
+        uint64_t ca = 0, cb = 0, cc = 0;
+        int cocc = 0, cemp = 0;
+        for (int j0 = 0; j0 < H; j0 += 32) {
+            const int j = j0 + lane;
+            const bool in = j < H;
+            const bool occ = in && ((h >> j) & 1ull);
+            const unsigned bo = __ballot_sync(0xffffffffu, occ);
+            const unsigned be = __ballot_sync(0xffffffffu, in && !occ);
+            const int io = cocc + __popc(bo & lt);        // occupied high orbits below j
+            uint64_t a = 0, b = 0, c = 0;
+            if (occ) {
+                const uint64_t *row = s.bin + j * NB;
+                a = row[k + io + 1];
+                b = row[k + io];
+                c = row[k + io + 2];
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t ta = __shfl_up_sync(0xffffffffu, a, o);
+                const uint64_t tb = __shfl_up_sync(0xffffffffu, b, o);
+                const uint64_t tc = __shfl_up_sync(0xffffffffu, c, o);
+                if (lane >= o) { a += ta; b += tb; c += tc; }
+            }
+            a += ca; b += cb; c += cc;
+            if (occ) {
+                s.sa[io + 1] = a;
+                s.sb[io + 1] = b;
+                s.sc[io + 1] = c;
+                s.pos[io] = j;
+            }
+            if (in && !occ) {
+                const int ie = cemp + __popc(be & lt);
+                s.emp[ie] = j;
+                s.eb[ie] = io;
+            }
+            ca = __shfl_sync(0xffffffffu, a, 31);
+            cb = __shfl_sync(0xffffffffu, b, 31);
+            cc = __shfl_sync(0xffffffffu, c, 31);
+            cocc += __popc(bo);
+            cemp += __popc(be);
+        }
+        if (lane == 0) s.sa[0] = s.sb[0] = s.sc[0] = 0ull;
+    }
+    __syncthreads();                              // prefix sums, positions, own block visible
+
+    const uint64_t SA = s.sa[ph];                 // base(h)
+    for (int t = tid; t < nhh; t += kThreads) {
+        const int a1 = t / nemp + 1, c = t - (a1 - 1) * nemp;
+        const int q = s.emp[c], b = s.eb[c];
+        const uint64_t *row = s.bin + q * NB;
+        const uint64_t bb = (a1 <= b) ? SA - (s.sa[b] - s.sa[a1 - 1]) + (s.sb[b] - s.sb[a1]) + row[k + b]
+                                      : SA - (s.sa[a1] - s.sa[b]) + (s.sc[a1 - 1] - s.sc[b]) + row[k + b + 1];
+        s.hh[t].base = bb;
+        s.hh[t].g = s.G[(L + q) * omega + (L + s.pos[a1 - 1])];
+    }
+    for (int a = tid; a < ph; a += kThreads) s.mxo[a] = (k < L) ? s.sc[a] + SA - s.sa[a + 1] : 0ull;
+    for (int c = tid; c < nemp; c += kThreads) {
+        const int b = s.eb[c];
+        s.mxe[c] = (k > 0) ? s.sb[b] + s.bin[s.emp[c] * NB + k + b] + SA - s.sa[b] : 0ull;
+    }
+
+    A Dh = A(0);
+    for (uint64_t w = h; w; w &= w - 1) Dh += s.d[L + __ffsll((long long)w) - 1];
+
+    uint32_t lr[R];
+    A acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        lr[i] = 0;
+        acc[i] = A(0);
+        if (r < nk) {
+            const uint32_t l = __ldg(lw + r);
+            lr[i] = l;
+            A D = A(0);
+            for (uint32_t w = l; w; w &= w - 1) D += s.d[__ffs(w) - 1];
+            acc[i] = (D + Dh) * A(s.x[r]);
+        }
+    }
+
+    // low -> low (own block, shared memory)
+    if (k > 0 && k < L) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (tid + i * kThreads < nk) {
+                const uint32_t l = lr[i];
+                A a = acc[i];
+                for (uint32_t oc = l; oc; oc &= oc - 1) {
+                    const int o = __ffs(oc) - 1;
+                    const uint32_t lo = l ^ (1u << o);
+                    const A *gcol = s.G + o;
+                    for (uint32_t em = ~l & maskL; em; em &= em - 1) {
+                        const int q = __ffs(em) - 1;
+                        a += gcol[q * omega] * A(s.x[s.rank[lo | (1u << q)]]);
+                    }
+                }
+                acc[i] = a;
+            }
+        }
+    }
+    __syncthreads();                              // hop tables visible
+
+    // The gathers below go to L2 or DRAM.  Each group issues kU independent
+    // loads before the multiply-adds that consume them, so a warp keeps kU
+    // requests in flight instead of waiting a full memory latency per hop.
+    constexpr int kU = (R >= 4) ? 4 : 8;
+    // high -> high: same offsets in the target block (coalesced)
+    for (int j0 = 0; j0 < nhh; j0 += kU) {
+        T v[kU][R];
+        A g[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + u;
+            const bool ok = j < nhh;
+            const T *xb = x + (ok ? s.hh[j].base : 0ull);
+            g[u] = ok ? s.hh[j].g : A(0);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = tid + i * kThreads;
+                v[u][i] = (ok && r < nk) ? __ldg(xb + r) : T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+            for (int i = 0; i < R; ++i) acc[i] += g[u] * A(v[u][i]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if (tid + i * kThreads >= nk) continue;
+        const uint32_t l = lr[i];
+        A a = acc[i];
+        // high -> low: occupied high orbit P_a to empty low orbit e (block h - P_a)
+        if (k < L) {
+            for (uint32_t em = ~l & maskL; em; em &= em - 1) {
+                const int e = __ffs(em) - 1;
+                const uint64_t off = s.rank[l | (1u << e)];
+                const A *grow = s.G + e * omega + L;
+                for (int a0 = 0; a0 < ph; a0 += kU) {
+                    T v[kU];
+                    A g[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int aa = a0 + u;
+                        const bool ok = aa < ph;
+                        v[u] = ok ? __ldg(x + s.mxo[aa] + off) : T(0);
+                        g[u] = ok ? grow[s.pos[aa]] : A(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) a += g[u] * A(v[u]);
+                }
+            }
+        }
+        // low -> high: occupied low orbit o to empty high orbit q (block h + q)
+        if (k > 0) {
+            for (uint32_t oc = l; oc; oc &= oc - 1) {
+                const int o = __ffs(oc) - 1;
+                const uint64_t off = s.rank[l ^ (1u << o)];
+                const A *gcol = s.G + L * omega + o;
+                for (int c0 = 0; c0 < nemp; c0 += kU) {
+                    T v[kU];
+                    A g[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int c = c0 + u;
+                        const bool ok = c < nemp;
+                        v[u] = ok ? __ldg(x + s.mxe[c] + off) : T(0);
+                        g[u] = ok ? gcol[s.emp[c] * omega] : A(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) a += g[u] * A(v[u]);
+                }
+            }
+        }
+        acc[i] = a;
+    }
+
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * kThreads;
+        if (r < nk) y[base + r] = T(acc[i]);
+    }
+    if (swdot) warp_dot<T, A, R>(acc, s.x, nk, swdot);
+}
+
+template <typename T, typename A, int R>
+__global__ void __launch_bounds__(kThreads)
+hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, const T *__restrict__ x,
+           T *__restrict__ y, Tickets *tk, const int *__restrict__ skip, double *blk_part, double *dot_out)
+{
+    if (skip && *skip) return;                    // CTA-uniform
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_next[2];
+    __shared__ double sred[kThreads / 32];
+    __shared__ double swdot[kThreads / 32];
+    const int omega = B.omega, L = B.L, H = B.H, N = B.n;
+    const Smem3<T, A> s(smem, layout3<T, A>(omega, L, H, N, B.max_block, B.max_hh));
+    const int tid = threadIdx.x;
+    for (int i = tid; i < omega * omega; i += kThreads) s.G[i] = Gg[i];
+    for (int i = tid; i < omega; i += kThreads) s.d[i] = dg[i];
+    for (int i = tid; i < (1 << L); i += kThreads) s.rank[i] = B.rankL[i];
+    for (int i = tid; i < (H > 0 ? H : 1) * (N + 2); i += kThreads) {
+        const int p = i / (N + 2), m = i - p * (N + 2);
+        s.bin[i] = __ldg(B.binom + (L + p) * kBinomStride + m);
+    }
+
+    if (tid == 0) s_next[0] = (long long)atomicAdd(&tk->hx_next, 1ull);
+    long long prev = -1;
+    for (int it = 0;; it ^= 1) {
+        __syncthreads();                          // smem of the previous block is free
+        const long long b = s_next[it];
+        if (tid == 0) {
+            block_sum_deferred(blk_part, prev, swdot);
+            if (b < B.nblocks) s_next[it ^ 1] = (long long)atomicAdd(&tk->hx_next, 1ull);
+        }
+        if (b >= B.nblocks) break;
+        hx3_block<T, A, R>(s, omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, x, y,
+                           blk_part ? swdot : nullptr);
+        prev = b;
+    }
+    hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
+}
+
 constexpr size_t kSmemLimit = 200 * 1024;
 
 // Variant 2 only on request (the autotuner's choice, or the caller's) and when
@@ -742,16 +1057,26 @@ bool use_v2(const Blocks &B)
     return layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total <= kSmemLimit;
 }
 
+// Variant 3 on request, when its shared memory fits (full space only)
+template <typename T, typename A>
+bool use_v3(const Blocks &B)
+{
+    if (B.variant != 3 || B.kept_map) return false;
+    return layout3<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total <= kSmemLimit;
+}
+
 template <typename T, typename A, int R>
 const void *kernel_fn(const Blocks &B)
 {
     if (B.kept_map) return (const void *)hx_kernel<T, A, R, true>;
+    if (use_v3<T, A>(B)) return (const void *)hx3_kernel<T, A, R>;
     return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R, false>;
 }
 
 template <typename T, typename A>
 size_t kernel_smem(const Blocks &B)
 {
+    if (use_v3<T, A>(B)) return layout3<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total;
     return use_v2<T, A>(B) ? layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total
                            : layout<T, A>(B.omega, B.L, B.H, B.max_block, B.max_hh).total;
 }
@@ -770,6 +1095,9 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     if (B.kept_map)
         hx_kernel<T, A, R, true><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                                static_cast<T *>(y), tk, skip, bp, out);
+    else if (use_v3<T, A>(B))
+        hx3_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                          static_cast<T *>(y), tk, skip, bp, out);
     else if (v2)
         hx2_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                           static_cast<T *>(y), tk, skip, bp, out);
@@ -1015,6 +1343,7 @@ size_t hx_smem_bytes(const Blocks &B, int precision)
 
 int hx_variant(const Blocks &B, int precision)
 {
+    if (precision == 0 ? use_v3<double, double>(B) : use_v3<float, float>(B)) return 3;
     return (precision == 0 ? use_v2<double, double>(B) : use_v2<float, float>(B)) ? 2 : 1;
 }
 
@@ -1052,8 +1381,6 @@ cudaError_t batch_launch_t(const BatchBlocks &BB, const A *G, const A *d, const 
     cudaError_t err = cudaFuncSetAttribute(batch_fn_rows<T, A>(rows),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-    if (err != cudaSuccess) return err;
     const T *xt = static_cast<const T *>(x);
     T *yt = static_cast<T *>(y);
     if (rows <= 1) hx_batch_kernel<T, A, 1><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
@@ -1082,9 +1409,9 @@ int batch_grid_t(const BatchBlocks &BB)
 }  // namespace
 
 cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
-                            int *counter, int grid, cudaStream_t st, const int *skip, int skip_stride)
+                            unsigned long long *counter, int grid, cudaStream_t st, const int *skip, int skip_stride)
 {
-    auto *ctr = reinterpret_cast<unsigned long long *>(counter);
+    unsigned long long *ctr = counter;
     if (precision == 0) return batch_launch_t<double, double>(BB, P.G64, P.d64, x, y, ctr, grid, st, skip, skip_stride);
     return batch_launch_t<float, float>(BB, P.G32, P.d32, x, y, ctr, grid, st, skip, skip_stride);
 }

@@ -277,9 +277,11 @@ struct HxProblem {
     const double *G64, *d64;         // G [omega*omega], d_p = 2 e_p + G_pp
     const float *G32, *d32;
 };
-// batched H*x: skip[p * skip_stride] != 0 passes over problem p (skip nullable)
+// batched H*x: skip[p * skip_stride] != 0 passes over problem p (skip nullable).
+// counter: two zeroed device counters (next block, finished CTAs); the last CTA
+// returns both to zero, so no memset is needed between launches (graph-safe).
 cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
-                            int *counter, int grid, cudaStream_t st, const int *skip, int skip_stride);
+                            unsigned long long *counter, int grid, cudaStream_t st, const int *skip, int skip_stride);
 int hx_batch_grid(const BatchBlocks &BB, int precision);
 size_t hx_smem_bytes(const Blocks &B, int precision);
 int hx_variant(const Blocks &B, int precision);   // kernel variant a launch will use (1 or 2)
@@ -396,6 +398,7 @@ struct BatchState {                  // one problem (device memory)
     double hist[4];                  // last restart residuals (stagnation test)
     int used, broken, done, skip;    // skip = done || broken (kernels pass over the problem)
     int iters, done_cycle, stalled, pad;
+    unsigned long long t_done;       // device clock (ns) when the problem's answer was final
 };
 struct BatchVec {                    // vectors concatenated over problems, cut into chunks
     int count;
@@ -435,13 +438,20 @@ cudaError_t seg_residual_launch(const BatchVec &V, const double *w, const double
                                 double *partials, cudaStream_t st);
 cudaError_t batch_reset_launch(BatchState *S, int count, cudaStream_t st);
 cudaError_t batch_finalize_launch(BatchState *S, int count, int i, cudaStream_t st);
-// after step 0 of a cycle: convergence / stagnation per problem; *active = problems still running
-cudaError_t batch_converge_launch(BatchState *S, int count, double tol, int cycle, int stall_check,
+// after step 0 of a cycle: convergence / stagnation per problem; *active += problems
+// still running; the cycle number is read from *cycle (device)
+cudaError_t batch_converge_launch(BatchState *S, int count, double tol, const int *cycle, int stall_check,
                                   int *active, cudaStream_t st);
+// end of a cycle's convergence test, one thread: the device-side loop condition
+// (problems still running and cycles left), then ctl[1] += 1 and ctl[0] = 0.
+// ctl[0] = running problems, ctl[1] = cycle number.
+cudaError_t batch_ctl_launch(int *ctl, int max_cycles, cudaGraphConditionalHandle loop, cudaStream_t st);
+// *t = the device clock in ns
+cudaError_t device_clock_launch(unsigned long long *t, cudaStream_t st);
 cudaError_t batch_tridiag_launch(BatchState *S, int count, cudaStream_t st);
 // after refinement: problems with rel > tol reopen (done = skip = 0), the others are
 // finished; *reopened = number reopened
-cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, int last_cycle, int *reopened,
+cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, const int *last_cycle, int *reopened,
                                 cudaStream_t st);
 // e0 = c2[0] / c2[1] (Rayleigh quotient from v^T w and v^T v)
 cudaError_t batch_rayleigh_launch(BatchState *S, int count, int stage, cudaStream_t st);

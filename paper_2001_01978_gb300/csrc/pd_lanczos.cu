@@ -897,13 +897,21 @@ __global__ void batch_finalize_kernel(BatchState *S, int count, int i)
     if (!(b > 1e-13 * tn)) { P.broken = 1; P.skip = 1; }
 }
 
-__global__ void batch_converge_kernel(BatchState *S, int count, double tol, int cycle, int stall_check,
-                                      int *active)
+__device__ __forceinline__ unsigned long long device_clock_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void batch_converge_kernel(BatchState *S, int count, double tol, const int *cycle_dev,
+                                      int stall_check, int *active)
 {
     const int pr = blockIdx.x * blockDim.x + threadIdx.x;
     if (pr >= count) return;
     BatchState &P = S[pr];
     if (P.done) return;
+    const int cycle = *cycle_dev;
     const double a = P.alpha[0], b = P.beta[0];
     const double rel = (b == 0.0) ? 0.0 : b / fabs(a);
     P.rel = rel;
@@ -918,9 +926,24 @@ __global__ void batch_converge_kernel(BatchState *S, int count, double tol, int 
         P.done = 1;
         P.skip = 1;
         P.done_cycle = cycle;
+        P.t_done = device_clock_ns();
     } else {
         atomicAdd(active, 1);
     }
+}
+
+__global__ void batch_ctl_kernel(int *ctl, int max_cycles, cudaGraphConditionalHandle loop)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int active = ctl[0], cycle = ctl[1];
+    cudaGraphSetConditional(loop, (active > 0 && cycle < max_cycles) ? 1u : 0u);
+    ctl[1] = cycle + 1;
+    ctl[0] = 0;
+}
+
+__global__ void device_clock_kernel(unsigned long long *t)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t = device_clock_ns();
 }
 
 __global__ void batch_tridiag_kernel(BatchState *S, int count)
@@ -936,13 +959,14 @@ __global__ void batch_tridiag_kernel(BatchState *S, int count)
 }
 
 // after the FP64 refinement: problems whose residual misses tol are reopened
-__global__ void batch_reopen_kernel(BatchState *S, int count, double tol, int last_cycle, int *reopened)
+__global__ void batch_reopen_kernel(BatchState *S, int count, double tol, const int *next_cycle, int *reopened)
 {
     const int pr = blockIdx.x * blockDim.x + threadIdx.x;
     if (pr >= count) return;
     BatchState &P = S[pr];
-    if (P.rel <= tol) {                          // refined residual within tol: finished
-        if (!P.done) { P.done = 1; P.skip = 1; P.done_cycle = last_cycle; }
+    if (P.rel <= tol) {                          // refined residual within tol: finished, the answer is final now
+        if (!P.done) { P.done = 1; P.skip = 1; P.done_cycle = *next_cycle - 1; }
+        P.t_done = device_clock_ns();
         return;
     }
     P.done = 0;
@@ -1308,12 +1332,24 @@ cudaError_t batch_finalize_launch(BatchState *S, int count, int i, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t batch_converge_launch(BatchState *S, int count, double tol, int cycle, int stall_check,
+cudaError_t batch_converge_launch(BatchState *S, int count, double tol, const int *cycle, int stall_check,
                                   int *active, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(active, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
     batch_converge_kernel<<<(count + 127) / 128, 128, 0, st>>>(S, count, tol, cycle, stall_check, active);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_ctl_launch(int *ctl, int max_cycles, cudaGraphConditionalHandle loop, cudaStream_t st)
+{
+    batch_ctl_kernel<<<1, 32, 0, st>>>(ctl, max_cycles, loop);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t device_clock_launch(unsigned long long *t, cudaStream_t st)
+{
+    device_clock_kernel<<<1, 32, 0, st>>>(t);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1325,7 +1361,7 @@ cudaError_t batch_tridiag_launch(BatchState *S, int count, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, int last_cycle, int *reopened,
+cudaError_t batch_reopen_launch(BatchState *S, int count, double tol, const int *last_cycle, int *reopened,
                                 cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(reopened, 0, sizeof(int), st);

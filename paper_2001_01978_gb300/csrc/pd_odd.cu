@@ -6,10 +6,12 @@
 // Eq. 2 restricted to those orbits.  Each subspace is therefore an ordinary
 // handle of this library on the reduced (e, G): the same basis tables, H*x
 // kernels and Lanczos run unchanged.  Block = 0 of the paper (block = -1
-// here) solves every b in turn and keeps the lowest; all handles have the
-// same sizes, so after the first one their device blocks come from the
-// library's cache.  The returned occupations put 1 on the blocked orbit
-// (N_Occup, Sec. 4.3).
+// here) needs every b: the Omega subspaces, all of the same size, are solved
+// together by the batched solver (pd_batch.cu) and the lowest E_b is kept;
+// when the caller wants its vector or occupations, that one subspace is
+// solved once more as a handle.  Start kinds the batch does not offer (the
+// paper's [1,0,...,0] and HF) solve the subspaces one after another.  The
+// returned occupations put 1 on the blocked orbit (N_Occup, Sec. 4.3).
 #include "pd_internal.h"
 #include "pairdiag.h"
 
@@ -78,7 +80,47 @@ extern "C" int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e
     std::vector<double> er(om);
     std::vector<double> Gr((size_t)om * om);
     int status = PD_OK;
-    const int b_lo = block < 0 ? 0 : block, b_hi = block < 0 ? omega - 1 : block;
+    int b_lo = block < 0 ? 0 : block, b_hi = block < 0 ? omega - 1 : block;
+    const bool batched = block < 0 && o.mode == 0 && (o.start == PD_START_RANDOM || o.start == PD_START_MLP);
+    if (batched) {
+        // every subspace in one batched solve
+        std::vector<int> oms(omega, om), ns(omega, n_pairs), st_b(omega);
+        std::vector<double> e_all((size_t)omega * om), G_all((size_t)omega * om * om), e0_b(omega);
+        std::vector<pairdiag_batch_result> res(omega);
+        for (int b = 0; b < omega; ++b)
+            for (int i = 0, r = 0; i < omega; ++i) {
+                if (i == b) continue;
+                e_all[(size_t)b * om + r] = e[i];
+                for (int j = 0, c = 0; j < omega; ++j) {
+                    if (j == b) continue;
+                    G_all[((size_t)b * om + r) * om + c] = G[i * omega + j];
+                    ++c;
+                }
+                ++r;
+            }
+        const int sb = pairdiag_batch_ground_state(omega, oms.data(), ns.data(), e_all.data(), G_all.data(), tol, &o,
+                                                   mlp, e0_b.data(), st_b.data(), res.data(), nullptr);
+        if (sb != PD_OK && sb != PD_ENOCONV) return sb;
+        if (sb == PD_ENOCONV) status = PD_ENOCONV;
+        for (int b = 0; b < omega; ++b) {
+            const double eb = e0_b[b] + e[b];
+            if (energies) energies[b] = eb;
+            if (best < 0 || eb < best_e) {
+                best = b;
+                best_e = eb;
+            }
+        }
+        const pairdiag_batch_result &rb = res[best];
+        best_info.dim = dim;
+        best_info.nnz_offdiag = dim * (int64_t)n_pairs * (int64_t)(om - n_pairs);
+        best_info.iterations = rb.iterations;
+        best_info.hx_products = rb.iterations;
+        best_info.converged = rb.converged;
+        best_info.rel_residual = rb.rel_residual;
+        best_info.gap_estimate = NAN;
+        if (!vec && !occ) b_hi = b_lo - 1;         // nothing more to compute
+        else b_lo = b_hi = best;                    // the winner once more, for its vector
+    }
     for (int b = b_lo; b <= b_hi; ++b) {
         for (int i = 0, r = 0; i < omega; ++i) {          // e and G on the orbits other than b
             if (i == b) continue;
@@ -103,8 +145,9 @@ extern "C" int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e
         }
         if (st == PD_ENOCONV) status = PD_ENOCONV;
         eb += e[b];
+        if (batched) eb = best_e;                  // E_b stays the batched solve's (the vector is this solve's)
         if (energies) energies[b] = eb;
-        if (best < 0 || eb < best_e) {
+        if (batched || best < 0 || eb < best_e) {
             if (occ) {
                 const int so = pairdiag_occupations_dev(h, static_cast<const double *>(buf.v[cur]), best_occ.data());
                 if (so != PD_OK) {

@@ -71,7 +71,7 @@ def test_workload_4096_stratified_subset():
     picks = [int(order[k]) for k in np.linspace(0, len(order) - 1, 12).astype(int)]
     golden = {int(row[0]): (int(row[1]), int(row[2]), float(row[4]))
               for row in read_golden("batch4096_s5_picks_e0.txt")}
-    assert sorted(golden) == sorted(i for i in picks if dims[i] > 20000)
+    assert sorted(golden) == sorted(picks)
     for i in picks:
         om, n, e, G = probs[i]
         if dims[i] <= 20000:

@@ -31,6 +31,18 @@ def solve(omega, n, e, G, tol=1e-12, **opt):
 
 
 # --------------------------------------------------------------- FP64 -------
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("omega,n,low", [(16, 5, 10), (18, 3, 9), (14, 7, 0)])
+def test_solver_hx_variants_fp64(omega, n, low, variant):
+    """Each H*x kernel variant inside the Lanczos step (its fused alpha dot
+    included): E0 against the oracle to 1e-10."""
+    e, G = pd_inputs.separable_noise(omega, seed=omega * 3 + n)
+    ref = oracle.lanczos_ground(omega, n, e, G, window=40, tol=1e-13)["e0"]
+    r = solve(omega, n, e, G, tol=1e-12, low_bits=low, hx_variant=variant)
+    assert r["status"] == pd.PD_OK
+    assert abs(r["e0"] - ref) <= 1e-10 * abs(ref)
+
+
 def test_config_omega12_fp64():
     omega, n, e, G = pd_inputs.workload("omega12_n6_picket")
     ref = oracle.lanczos_ground(omega, n, e, G, window=50, tol=1e-13)
