@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solves")
+    ap.add_argument("--truncate", action="store_true",
+                    help="truncated model space (Sec. 3.5): E0 and time at nested Dimension_Limit values")
     ap.add_argument("--hx-only", action="store_true",
                     help="time only the H*x kernel (profiling aid; not the benchmark line)")
     ap.add_argument("--omega", type=int, default=0, help="with --hx-only: picket-fence size instead of --workload")
@@ -649,6 +651,61 @@ def run_forms(args, workload, tag):
     return 0
 
 
+def run_truncate(args):
+    """The truncated model space of Sec. 3.5 on the Omega=28, N=14 separable
+    workload (seed 1, dim 4.0e7): for nested Dimension_Limit values, the kept
+    dimension, the set-up time of the truncation (diagonal histogram and kept
+    map), the time of one truncated FP32 H*x, the time to E0 of the mixed form
+    and E0 against the full-space E0 (the convergence Sec. 5.4 studies)."""
+    import torch
+    import paper_2001_01978_gb300 as pd
+    torch.cuda.set_device(0)
+    omega, n = 28, 14
+    e, G = pd_inputs.separable_noise(omega, seed=1)
+    dim = math.comb(omega, n)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    clocks = ClockSampler(0)
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=args.window, seed=1) as s:
+        pd.pairdiag_set_stream(s.h, stream)
+        full = pd.pairdiag_ground_state_dev(s.h, 1e-9, None)
+        for limit in (10 ** 5, 10 ** 6, 4 * 10 ** 6, 10 ** 7, 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kept = pd.pairdiag_truncate(s.h, limit)
+            t_setup = time.perf_counter() - t0
+            x = torch.randn(kept, dtype=torch.float32, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(2):
+                pd.pairdiag_hx_dev(s.h, pd.PD_PREC_MIXED, x, y)
+            hx_ms = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                pd.pairdiag_hx_dev(s.h, pd.PD_PREC_MIXED, x, y)
+                ev1.record(stream)
+                ev1.synchronize()
+                hx_ms.append(ev0.elapsed_time(ev1))
+            del x, y
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = pd.pairdiag_ground_state_dev(s.h, 1e-9, None)
+            ev1.record(stream)
+            ev1.synchronize()
+            rows.append({"dimension_limit": limit or None, "kept_dim": kept, "nnz": pd.pairdiag_nnz(s.h),
+                         "setup_s": t_setup, "hx_ms": statistics.median(hx_ms),
+                         "hx_nnz_per_s": pd.pairdiag_nnz(s.h) / (statistics.median(hx_ms) * 1e-3),
+                         "time_to_e0_ms": ev0.elapsed_time(ev1), "iterations": r["iterations"], "e0": r["e0"],
+                         "e0_minus_full": r["e0"] - full["e0"], "status": r["status"]})
+    clk = clocks.stop()
+    print(json.dumps({"truncation": True, "workload": "omega28_n14_sepnoise_s1", "dim": dim, "tol": 1e-9,
+                      "form": "mixed", "bins": 10 ** 8, "full_e0": full["e0"], "limits": rows, "clocks": clk}))
+    return 0
+
+
 def run_batch(args):
     """Batched form: 4096 Hamiltonians (Omega ~ U{10..22}, N = Omega/2 +- U{0..3}) in
     one lock-step solve, mixed form vs plain FP64, same tolerance."""
@@ -763,6 +820,7 @@ def run_odd(args):
 def main():
     args = parse_args()
     mode = ("batch" if args.batch else "warm" if args.warm else "big" if args.big else "odd" if args.odd else
+            "truncate" if args.truncate else
             "hx" if args.hx_only and args.impl != "reference" else "line")
     if args.steps is None:
         args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10, "odd": 3}.get(mode, 30)
@@ -776,6 +834,8 @@ def main():
         return run_big(args)
     if args.odd:
         return run_odd(args)
+    if args.truncate:
+        return run_truncate(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

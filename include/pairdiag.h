@@ -80,9 +80,11 @@ typedef struct {
     int      hx_variant;    /* H*x kernel: 0 = automatic (default, currently 1), 1 = neighbour
                                blocks staged one at a time, 2 = all neighbour blocks staged at
                                once, 3 = no staging, every target gathered from global memory
-                               (for small blocks, far from half filling); 2 and 3 fall back
-                               to 1 when their shared memory does not fit.  A truncated
-                               handle (pairdiag_truncate) runs variant 1 */
+                               with O(1) hop tables, 4 = variant 3 with the gathers issued in
+                               deep groups (far from half filling, where a thread has one row
+                               and x is in DRAM); 2-4 fall back to 1 when their shared memory
+                               does not fit.  A truncated handle (pairdiag_truncate) runs
+                               variant 1 */
 } pairdiag_options;
 
 typedef struct {
@@ -262,7 +264,10 @@ int pairdiag_occupations_dev(pairdiag_t *h, const double *v_dev, double *occ);
  * component; this warm start is an addition of this library.  A network maps
  * per-orbit features of (e, G, N) to weights w_i; the start vector is
  * psi(s) = exp(sum_{i in s} w_i - max).  Network: 16 -> 128 -> 128 -> 128 -> 1,
- * SiLU, bfloat16 operands with FP32 accumulation, FP32 master weights, Adam.
+ * SiLU, bfloat16 operands with FP32 accumulation on the tensor cores
+ * (tcgen05.mma, accumulators in tensor memory), FP32 master weights, Adam.
+ * The entry points that run the network return PD_ETIMEOUT if a product's
+ * bounded wait for its tensor-core operations expired.
  * Parameters (pairdiag_mlp_num_params() floats) are packed as W1 [16x128],
  * b1 [128], W2 [128x128], b2, W3 [128x128], b3, w4 [128], b4 [1], row-major.
  */
@@ -286,6 +291,25 @@ int  pairdiag_mlp_loss_grad(pairdiag_mlp_t *m, int rows, const float *X, const f
 /* `steps` full-batch Adam steps on (X, target); loss_history host [steps], nullable. */
 int  pairdiag_mlp_train(pairdiag_mlp_t *m, int rows, const float *X, const float *target, int steps,
                         double lr, double *loss_history);
+/* Intermediates of the network's last forward (and backward) pass, for
+ * checking each layer on its own (test hook; the paper has no network):
+ * which = PD_MLP_*, rows = the rows of that pass.  Activations and backward
+ * intermediates stored in bfloat16 are widened to float.  out: host [rows *
+ * 128] floats (PD_MLP_OUT, PD_MLP_DOUT: [rows]).  Synchronous. */
+#define PD_MLP_Z1   0    /* X W1 + b1, FP32 */
+#define PD_MLP_A1   1    /* silu(Z1), bfloat16 */
+#define PD_MLP_Z2   2
+#define PD_MLP_A2   3
+#define PD_MLP_Z3   4
+#define PD_MLP_A3   5
+#define PD_MLP_OUT  6    /* A3 w4 + b4, FP32 */
+#define PD_MLP_DOUT 7    /* 2 (out - t) / rows, FP32 (after a loss/gradient pass) */
+#define PD_MLP_DZ3  8    /* dout w4 silu'(Z3), bfloat16 */
+#define PD_MLP_DA2  9    /* dZ3 W3^T, FP32 */
+#define PD_MLP_DZ2  10   /* dA2 silu'(Z2), bfloat16 */
+#define PD_MLP_DA1  11   /* dZ2 W2^T, FP32 */
+#define PD_MLP_DZ1  12   /* dA1 silu'(Z1), bfloat16 */
+int  pairdiag_mlp_buffer(const pairdiag_mlp_t *m, int which, int rows, float *out);
 /* Use the network for PD_START_MLP (the handle keeps the pointer; nullptr clears). */
 int  pairdiag_set_mlp(pairdiag_t *h, pairdiag_mlp_t *m);
 /* Use fixed weights w (host [omega]) for PD_START_MLP when no network is set. */
@@ -356,12 +380,15 @@ int pairdiag_batch_ground_state(int count, const int *omega, const int *n_pairs,
  * with b blocked is the seniority-zero space of n_pairs pairs on the other
  * omega-1 orbits, and
  *     E_b = e_b + E0(Eq. 2 with e and G restricted to the orbits i != b).
- * With block = -1 and a PD_START_RANDOM or PD_START_MLP start, all omega
- * subspaces (of equal size) are solved together by the batched solver
+ * Subspaces of at most 2^17 states with block = -1 and a PD_START_RANDOM or
+ * PD_START_MLP start are solved together by the batched solver
  * (pairdiag_batch_ground_state) and, when vec or occ is wanted, the winning
  * subspace once more as a handle for its vector and occupations (e0 and
- * energies stay those of the batched solve; info describes the second solve).  Otherwise each subspace is a handle of this library on the
- * restricted (e, G), solved in turn.  Everything runs on the current device.
+ * energies stay those of the batched solve; info describes the second solve).
+ * Otherwise each subspace is a handle of this library on the restricted
+ * (e, G); with block = -1 up to three library-internal host threads solve
+ * them at once, each on a stream of its own.  Everything runs on the device
+ * current when the call is made.
  *   omega, n_pairs : omega in 2..62, n_pairs in 0..omega-1 (2*n_pairs+1 particles)
  *   e, G           : host, as in pairdiag_create (G exactly symmetric)
  *   block          : -1 = every b, the lowest E_b is returned (the paper's Block = 0);
@@ -392,7 +419,7 @@ int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e, const dou
 /*
  * H*x schedule autotuner (an addition of this library; the paper has a single
  * CPU code path).  For one problem and precision it times the H*x kernel for
- * every block split L = low_bits in [min(omega,8), min(omega,13)] and the three
+ * every block split L = low_bits in [min(omega,8), min(omega,13)] and the four
  * kernel variants (median of `reps` launches on a random vector, CUDA events)
  * and records the fastest (low_bits, hx_variant) for (omega, n_pairs,
  * precision) in a process-wide table.  pairdiag_create and the batched solver
@@ -486,7 +513,7 @@ int pairdiag_tridiag_lowest(pairdiag_t *h, int m, const double *alpha, const dou
  * whole device, which a latency-critical host loop cannot afford, and some
  * host applications give a library no device memory beyond the buffers they
  * pass in.  This entry point needs no handle and calls no allocating routine:
- * its partial sums go to a fixed device array inside the library (311,296
+ * its partial sums go to a fixed device array inside the library (524,288
  * bytes, held on every GPU that loads the library until the process exits).
  *
  *   out_dev[j] = sum_{i<n} Q_dev[j*ld + i] * p_dev[i],  j < m,  FP64 accumulation

@@ -65,6 +65,27 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
+int sm_count()
+{
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    if (dev >= 0) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    if (dev >= 0) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 uint64_t host_binom(int n, int m)
 {
     static uint64_t table[64][64];
@@ -115,6 +136,7 @@ struct pairdiag {
     int64_t dim = 0, nnz = 0;        // of the space the solver works in (kept states when truncated)
     int64_t full_dim = 0, full_nnz = 0;   // C(Omega, N) and its off-diagonal nonzeros
     int32_t *d_kmap = nullptr;       // truncated space (Sec. 3.5): full index -> kept index, -1 dropped
+    uint64_t *d_kblk_h = nullptr, *d_kblk_base = nullptr;   // the blocks holding kept states
     Blocks B{};
     int device = 0;
     cudaStream_t st = nullptr;
@@ -167,10 +189,11 @@ void free_all(pairdiag *h)
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64,
-                    h->d_L64, h->d_L32, h->d_lockc, h->d_kmap};
+                    h->d_L64, h->d_L32, h->d_lockc, h->d_kmap, h->d_kblk_h, h->d_kblk_base};
     // the blocks go back to the library's cache: no queued kernel may still use
-    // them (cudaFree gave the same guarantee by synchronising the device)
-    cudaDeviceSynchronize();
+    // them.  Every kernel and copy of the handle runs on its stream, so that
+    // stream's completion is enough (other streams of the caller go on).
+    cudaStreamSynchronize(h->st);
     for (void *p : ptrs) pool_free(p);
 }
 
@@ -687,7 +710,7 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     if (o.mode != 0 && o.mode != 1) return fail(PD_EINVAL, "bad mode");
     if (o.low_bits < 0 || o.low_bits > kMaxLow) return fail(PD_EINVAL, "low_bits outside 0..%d", kMaxLow);
     if (o.max_restarts < 0) return fail(PD_EINVAL, "max_restarts < 0");
-    if (o.hx_variant < 0 || o.hx_variant > 3) return fail(PD_EINVAL, "hx_variant outside 0..3");
+    if (o.hx_variant < 0 || o.hx_variant > 4) return fail(PD_EINVAL, "hx_variant outside 0..4");
     if (o.start < PD_START_RANDOM || o.start > PD_START_MLP) return fail(PD_EINVAL, "bad start kind");
 
     if (o.low_bits == 0 && o.hx_variant == 0) {   // an autotuned schedule, if one was recorded
@@ -719,7 +742,7 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
         h->ldq = (h->dim + 3) / 4 * 4;
         h->hxgrid[0] = hx_grid(h->B, 0);
         h->hxgrid[1] = hx_grid(h->B, 1);
-        h->rgrid = (int)std::min<int64_t>(h->B.nblocks, 152 * 4);
+        h->rgrid = (int)std::min<int64_t>(h->B.nblocks, vec_grid());
         h->part_count = (size_t)std::max(vec_grid(), h->rgrid) * kMaxWindow;
         if ((st = dalloc(&h->d_part, h->part_count)) != PD_OK) break;
         if ((st = dalloc(&h->d_S, 1)) != PD_OK) break;
@@ -739,7 +762,6 @@ void pairdiag_destroy(pairdiag_t *h)
 {
     if (!h) return;
     cudaSetDevice(h->device);
-    if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     free_all(h);
     delete h;
 }
@@ -978,7 +1000,8 @@ void drop_space(pairdiag *h)
 {
     cudaStreamSynchronize(h->st);
     void **vecs[] = {&h->d_Q[0], &h->d_Q[1], &h->d_p[0], &h->d_p[1], (void **)&h->d_v64, (void **)&h->d_w64,
-                     (void **)&h->d_L64, (void **)&h->d_L32, (void **)&h->d_kmap};
+                     (void **)&h->d_L64, (void **)&h->d_L32, (void **)&h->d_kmap, (void **)&h->d_kblk_h,
+                     (void **)&h->d_kblk_base};
     for (void **v : vecs) {
         pool_free(*v);
         *v = nullptr;
@@ -988,6 +1011,8 @@ void drop_space(pairdiag *h)
     h->n_locked = 0;
     h->start.clear();
     h->B.kept_map = nullptr;
+    h->B.kept_blk_h = h->B.kept_blk_base = nullptr;
+    h->B.kept_nblocks = 0;
     h->dim = h->full_dim;
     h->nnz = h->full_nnz;
     h->ldq = (h->dim + 3) / 4 * 4;
@@ -1074,7 +1099,20 @@ int build_truncation(pairdiag *h, int64_t limit, int64_t bins, int64_t *kept)
         PD_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice, st));
         PD_TRY(dalloc(&h->d_kmap, (size_t)full));
         PD_CUDA(trunc_map_launch(B, h->d_d64, lo, hi, bins, cut, d_first, h->d_kmap, grid, st));
+        // the blocks that hold kept states, for the truncated H*x to walk
+        std::vector<uint64_t> bh(cnt.size()), bb(cnt.size());
+        PD_CUDA(cudaMemcpyAsync(bh.data(), B.blk_h, sizeof(uint64_t) * bh.size(), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaMemcpyAsync(bb.data(), B.blk_base, sizeof(uint64_t) * bb.size(), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaStreamSynchronize(st));
+        std::vector<uint64_t> kh, kb;
+        for (size_t b = 0; b < cnt.size(); ++b)
+            if (cnt[b] > 0) {
+                kh.push_back(bh[b]);
+                kb.push_back(bb[b]);
+            }
+        PD_TRY(upload(&h->d_kblk_h, kh));
+        PD_TRY(upload(&h->d_kblk_base, kb));
+        h->B.kept_nblocks = (int64_t)kh.size();
         return PD_OK;
     }();
     cleanup();
@@ -1099,6 +1137,8 @@ int pairdiag_truncate(pairdiag_t *h, int64_t dimension_limit, int64_t bins, int6
         h->dim = kept;
         h->ldq = (kept + 3) / 4 * 4;
         h->B.kept_map = h->d_kmap;
+        h->B.kept_blk_h = h->d_kblk_h;
+        h->B.kept_blk_base = h->d_kblk_base;
         h->hxgrid[0] = hx_grid(h->B, 0);
         h->hxgrid[1] = hx_grid(h->B, 1);
         // off-diagonal nonzeros of the truncated matrix: H x with every G_ij = 1
@@ -1195,7 +1235,7 @@ int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int L = lmin; L <= lmax && rc == PD_OK; ++L) {
-        for (int variant = 1; variant <= 3 && rc == PD_OK; ++variant) {
+        for (int variant = 1; variant <= 4 && rc == PD_OK; ++variant) {
             pairdiag_options o;
             pairdiag_default_options(&o);
             o.low_bits = L;
@@ -1250,7 +1290,7 @@ int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, 
 
 int pairdiag_tune_set(int omega, int n_pairs, int precision, int low_bits, int hx_variant_)
 {
-    if (low_bits < 0 || low_bits > kMaxLow || hx_variant_ < 0 || hx_variant_ > 3) return fail(PD_EINVAL, "bad schedule");
+    if (low_bits < 0 || low_bits > kMaxLow || hx_variant_ < 0 || hx_variant_ > 4) return fail(PD_EINVAL, "bad schedule");
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     if (low_bits == 0) g_tune.erase(TuneKey{omega, n_pairs, precision});
     else g_tune[TuneKey{omega, n_pairs, precision}] = {low_bits, hx_variant_};
@@ -1347,13 +1387,13 @@ int pairdiag_fma_peak(int precision, int reps, void *stream, double *tflops)
 // cudaMalloc/cudaFree, with their implicit device-wide synchronisation, is not
 // acceptable, or an application that hands this library no memory beyond the
 // buffers it passes) can still use it.  Every GPU that loads the library holds
-// the array (kNoAllocScratchDoubles doubles, 311,296 bytes) until the process
+// the array (kNoAllocScratchDoubles doubles, 524,288 bytes) until the process
 // exits.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
-constexpr int kNoAllocScratchDoubles = 152 * 4 * kMaxWindow;   // one row of kMaxWindow per streaming CTA
+constexpr int kNoAllocScratchDoubles = kMaxVecGrid * kMaxWindow;   // one row of kMaxWindow per streaming CTA
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 std::mutex g_noalloc_mutex;

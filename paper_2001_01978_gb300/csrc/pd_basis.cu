@@ -54,7 +54,7 @@ __global__ void rank_kernel(int omega, int n, const uint64_t *__restrict__ binom
 int grid_for(int64_t count)
 {
     int64_t g = (count + 255) / 256;
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > sm_count() * 32) g = sm_count() * 32;
     return (int)(g > 0 ? g : 1);
 }
 

@@ -178,12 +178,14 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
 
     uint32_t lr[R];
     A acc[R];
+    bool act[R];                              // rows of this thread that are computed (kept, if truncated)
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int r = tid + i * kThreads;
         lr[i] = 0;
         acc[i] = A(0);
-        if (r < nk) {
+        act[i] = r < nk && (!TR || __ldg(map + base + r) >= 0);
+        if (act[i]) {
             const uint32_t l = lw[r];
             lr[i] = l;
             A D = A(0);
@@ -196,7 +198,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
     if (k > 0 && k < L) {
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            if (tid + i * kThreads < nk) {
+            if (act[i]) {
                 const uint32_t l = lr[i];
                 A a = acc[i];
                 uint32_t occ = l;
@@ -216,15 +218,16 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         }
     }
 
-    // high -> high: same offsets in the target block
-    for (int j = 0; j < nhh; ++j) {
+    // high -> high: same offsets in the target block (warps without rows skip it)
+    const bool has_rows = (int)(tid & ~31) < nk;
+    for (int j = 0; has_rows && j < nhh; ++j) {
         const T *xb = x + sHH[j].base;
         const A g = sHH[j].g;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = tid + i * kThreads;
             if constexpr (TR) {
-                if (r < nk) acc[i] += g * A(x_kept(x, map, sHH[j].base + r));
+                if (act[i]) acc[i] += g * A(x_kept(x, map, sHH[j].base + r));
             } else {
                 if (r < nk) acc[i] += g * A(__ldg(xb + r));
             }
@@ -245,7 +248,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         if (occ_t) {                           // pair: high orbit go -> empty low orbit q
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                if (tid + i * kThreads < nk) {
+                if (act[i]) {
                     const uint32_t l = lr[i];
                     A a = acc[i];
                     uint32_t emp = ~l & maskL;
@@ -260,7 +263,7 @@ __device__ __forceinline__ void hx_block(const int omega, const int L, const int
         } else {                               // pair: occupied low orbit o -> high orbit go
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                if (tid + i * kThreads < nk) {
+                if (act[i]) {
                     const uint32_t l = lr[i];
                     A a = acc[i];
                     uint32_t occ = l;
@@ -303,6 +306,10 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
     __shared__ double sred[kThreads / 32];
     __shared__ double swdot[kThreads / 32];
     const int omega = B.omega, L = B.L, H = B.H, N = B.n;
+    // a truncated space walks only the blocks that hold kept states
+    const int64_t nb = TR ? B.kept_nblocks : B.nblocks;
+    const uint64_t *__restrict__ bh = TR ? B.kept_blk_h : B.blk_h;
+    const uint64_t *__restrict__ bbase = TR ? B.kept_blk_base : B.blk_base;
     const Layout lay = layout<T, A>(omega, L, H, B.max_block, B.max_hh);
     A *sG = reinterpret_cast<A *>(smem + lay.G);
     A *sd = reinterpret_cast<A *>(smem + lay.d);
@@ -326,15 +333,15 @@ hx_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
         const long long b = s_next[it];
         if (tid == 0) {
             block_sum_deferred(blk_part, prev, swdot);
-            if (b < B.nblocks) s_next[it ^ 1] = (long long)atomicAdd(&tk->hx_next, 1ull);
+            if (b < nb) s_next[it ^ 1] = (long long)atomicAdd(&tk->hx_next, 1ull);
         }
-        if (b >= B.nblocks) break;
+        if (b >= nb) break;
 
-        hx_block<T, A, R, TR>(omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, B.binom,
+        hx_block<T, A, R, TR>(omega, L, H, N, __ldg(bh + b), __ldg(bbase + b), B.lowword, B.binom,
                               sG, sd, sRank, sx, sxn, sHH, sMX, x, y, blk_part ? swdot : nullptr, B.kept_map);
         prev = b;
     }
-    hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
+    hx_finish(tk, nb, blk_part, dot_out, sred);
 }
 
 // ---- batched: blocks of many problems in one launch ----------------------------
@@ -601,8 +608,9 @@ __device__ __forceinline__ void hx2_block(const Smem2<T, A> &s, const int omega,
         }
     }
 
-    // high -> high: same offsets in the target block
-    for (int j = 0; j < nhh; ++j) {
+    // high -> high: same offsets in the target block (warps without rows skip it)
+    const bool has_rows = (int)(tid & ~31) < nk;
+    for (int j = 0; has_rows && j < nhh; ++j) {
         const T *xb = x + s.hh[j].base;
         const A g = s.hh[j].g;
 #pragma unroll
@@ -751,7 +759,7 @@ hx2_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg,
 // with q an empty high orbit and b the number of occupied high orbits below q:
 // the pairs between the moved ones change ordinal by one, the others keep it.
 struct Layout3 {
-    size_t g, d, rank, bin, x, hh, mxo, mxe, sa, sb, sc, pos, emp, eb, total;
+    size_t g, d, rank, bin, x, hp, hg, xo, xe, gs, ge, sa, sb, sc, pos, emp, eb, part, total;
 };
 
 template <typename T, typename A>
@@ -760,54 +768,269 @@ __host__ __device__ inline Layout3 layout3(int omega, int L, int H, int N, int m
     Layout3 s;
     size_t off = 0;
     const int h1 = H > 0 ? H : 1;
+    const int hh1 = max_hh > 0 ? max_hh : 1;
     s.g = off;    off = align16(off + sizeof(A) * omega * omega);
     s.d = off;    off = align16(off + sizeof(A) * omega);
     s.rank = off; off = align16(off + sizeof(uint16_t) * (size_t(1) << L));
     s.bin = off;  off = align16(off + sizeof(uint64_t) * h1 * (N + 2));
     s.x = off;    off = align16(off + sizeof(T) * max_block);
-    s.hh = off;   off = align16(off + sizeof(HHop<A>) * (max_hh > 0 ? max_hh : 1));
-    s.mxo = off;  off = align16(off + sizeof(uint64_t) * h1);
-    s.mxe = off;  off = align16(off + sizeof(uint64_t) * h1);
+    s.hp = off;   off = align16(off + sizeof(const T *) * hh1);
+    s.hg = off;   off = align16(off + sizeof(A) * hh1);
+    s.xo = off;   off = align16(off + sizeof(const T *) * h1);
+    s.xe = off;   off = align16(off + sizeof(const T *) * h1);
+    s.gs = off;   off = align16(off + sizeof(A) * h1 * L);
+    s.ge = off;   off = align16(off + sizeof(A) * h1 * L);
     s.sa = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
     s.sb = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
     s.sc = off;   off = align16(off + sizeof(uint64_t) * (h1 + 1));
     s.pos = off;  off = align16(off + sizeof(int) * h1);
     s.emp = off;  off = align16(off + sizeof(int) * h1);
     s.eb = off;   off = align16(off + sizeof(int) * h1);
+    s.part = off; off = align16(off + sizeof(A) * kThreads);
     s.total = off;
     return s;
 }
 
+// Shared-memory view of variant 3.  Per block: hp/hg the high->high targets
+// (pointer to the target block, coefficient); xo[a] the block h - P_a and
+// xe[c] the block h + q_c (pointers); gs[a*L + e] = G_{e, L+P_a} and
+// ge[c*L + o] = G_{L+q_c, o}, the coefficients of the high<->low hops.
 template <typename T, typename A>
 struct Smem3 {
-    A *G, *d;
+    A *G, *d, *hg, *gs, *ge, *part;
     uint16_t *rank;
-    uint64_t *bin, *mxo, *mxe, *sa, *sb, *sc;
+    uint64_t *bin, *sa, *sb, *sc;
     int *pos, *emp, *eb;
     T *x;
-    HHop<A> *hh;
+    const T **hp, **xo, **xe;
     __device__ Smem3(unsigned char *m, const Layout3 &l)
-        : G(reinterpret_cast<A *>(m + l.g)), d(reinterpret_cast<A *>(m + l.d)),
-          rank(reinterpret_cast<uint16_t *>(m + l.rank)), bin(reinterpret_cast<uint64_t *>(m + l.bin)),
-          mxo(reinterpret_cast<uint64_t *>(m + l.mxo)), mxe(reinterpret_cast<uint64_t *>(m + l.mxe)),
-          sa(reinterpret_cast<uint64_t *>(m + l.sa)), sb(reinterpret_cast<uint64_t *>(m + l.sb)),
-          sc(reinterpret_cast<uint64_t *>(m + l.sc)), pos(reinterpret_cast<int *>(m + l.pos)),
-          emp(reinterpret_cast<int *>(m + l.emp)), eb(reinterpret_cast<int *>(m + l.eb)),
-          x(reinterpret_cast<T *>(m + l.x)), hh(reinterpret_cast<HHop<A> *>(m + l.hh))
+        : G(reinterpret_cast<A *>(m + l.g)), d(reinterpret_cast<A *>(m + l.d)), hg(reinterpret_cast<A *>(m + l.hg)),
+          gs(reinterpret_cast<A *>(m + l.gs)), ge(reinterpret_cast<A *>(m + l.ge)),
+          part(reinterpret_cast<A *>(m + l.part)), rank(reinterpret_cast<uint16_t *>(m + l.rank)),
+          bin(reinterpret_cast<uint64_t *>(m + l.bin)), sa(reinterpret_cast<uint64_t *>(m + l.sa)),
+          sb(reinterpret_cast<uint64_t *>(m + l.sb)), sc(reinterpret_cast<uint64_t *>(m + l.sc)),
+          pos(reinterpret_cast<int *>(m + l.pos)), emp(reinterpret_cast<int *>(m + l.emp)),
+          eb(reinterpret_cast<int *>(m + l.eb)), x(reinterpret_cast<T *>(m + l.x)),
+          hp(reinterpret_cast<const T **>(m + l.hp)), xo(reinterpret_cast<const T **>(m + l.xo)),
+          xe(reinterpret_cast<const T **>(m + l.xe))
     {
     }
 };
 
-// One basis block of y = H x in variant 3.  Called by every thread after a
-// barrier that frees the previous block's shared memory; one barrier inside.
+// Small blocks (at most 32 rows, far from half filling): lane r of every warp
+// takes row r, and warp w the hops of class index w, w + 8, ...; warp 0 adds
+// the eight partial sums in warp order (a fixed order).  acc[0] of warp 0
+// holds the row's diagonal and low->low terms on entry and the row's y on
+// exit; y is written here.
 template <typename T, typename A, int R>
+__device__ __forceinline__ void hx3_small(const Smem3<T, A> &s, const int L, const int k, const int ph,
+                                          const int nemp, const int nhh, const uint64_t base,
+                                          const uint16_t *__restrict__ lw, T *__restrict__ y, const int nk,
+                                          A (&acc)[R])
+{
+    constexpr int kW = kThreads / 32;
+    const int tid = threadIdx.x, w = tid >> 5, r = tid & 31;
+    const uint32_t maskL = (1u << L) - 1u;
+    A a = (w == 0) ? acc[0] : A(0);
+    if (r < nk) {
+        const uint32_t l = __ldg(lw + r);
+#pragma unroll 2
+        for (int j = w; j < nhh; j += kW) a += s.hg[j] * A(__ldg(s.hp[j] + r));
+        if (k < L)
+            for (int ai = w; ai < ph; ai += kW) {
+                const T *xb = s.xo[ai];
+                const A *g = s.gs + ai * L;
+                uint32_t em = ~l & maskL;
+                for (int t = 0; t < L - k; ++t) {
+                    const int e = __ffs(em) - 1;
+                    em &= em - 1;
+                    a += g[e] * A(__ldg(xb + s.rank[l | (1u << e)]));
+                }
+            }
+        if (k > 0)
+            for (int c = w; c < nemp; c += kW) {
+                const T *xb = s.xe[c];
+                const A *g = s.ge + c * L;
+                uint32_t oc = l;
+                for (int t = 0; t < k; ++t) {
+                    const int o = __ffs(oc) - 1;
+                    oc &= oc - 1;
+                    a += g[o] * A(__ldg(xb + s.rank[l ^ (1u << o)]));
+                }
+            }
+    }
+    s.part[tid] = a;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = A(0);
+    if (w == 0 && r < nk) {
+        A t = A(0);
+#pragma unroll
+        for (int q = 0; q < kW; ++q) t += s.part[q * 32 + r];
+        acc[0] = t;
+        y[base + r] = T(t);
+    }
+}
+
+// The rows of one block in variant 3 (RR rows per thread): diagonal, low->low
+// from the staged block, then the gathers; writes y and the fused dot.
+template <typename T, typename A, int RR, bool DEEP>
+__device__ __forceinline__ void hx3_rows(const Smem3<T, A> &s, const int omega, const int L, const uint64_t h,
+                                         const uint64_t base, const uint16_t *__restrict__ lw,
+                                         T *__restrict__ y, double *swdot, const int k, const int ph,
+                                         const int nemp, const int nhh, const int nk)
+{
+    const int tid = threadIdx.x;
+    const uint32_t maskL = (1u << L) - 1u;
+    A Dh = A(0);
+    for (uint64_t w = h; w; w &= w - 1) Dh += s.d[L + __ffsll((long long)w) - 1];
+    uint32_t lr[RR];
+    A acc[RR];
+#pragma unroll
+    for (int i = 0; i < RR; ++i) {
+        const int r = tid + i * kThreads;
+        lr[i] = 0;
+        acc[i] = A(0);
+        if (r < nk) {
+            const uint32_t l = __ldg(lw + r);
+            lr[i] = l;
+            A D = A(0);
+            for (uint32_t w = l; w; w &= w - 1) D += s.d[__ffs(w) - 1];
+            acc[i] = (D + Dh) * A(s.x[r]);
+            // low -> low (own block, shared memory)
+            A a = acc[i];
+            uint32_t oc = l;
+            for (int u = 0; u < k; ++u) {
+                const int o = __ffs(oc) - 1;
+                oc &= oc - 1;
+                const uint32_t lo = l ^ (1u << o);
+                const A *gcol = s.G + o;
+                uint32_t em = ~l & maskL;
+                for (int v = 0; v < L - k; ++v) {
+                    const int q = __ffs(em) - 1;
+                    em &= em - 1;
+                    a += gcol[q * omega] * A(s.x[s.rank[lo | (1u << q)]]);
+                }
+            }
+            acc[i] = a;
+        }
+    }
+    if (nk <= 32) {                               // block-uniform
+        hx3_small<T, A, RR>(s, L, k, ph, nemp, nhh, base, lw, y, nk, acc);
+        if (swdot) warp_dot<T, A, RR>(acc, s.x, nk, swdot);
+        return;
+    }
+    // warps without a row of this block skip the gathers (warp-uniform)
+    if ((int)(tid & ~31) < nk) {
+        // high -> high: same offsets in the target block (coalesced).  Deep
+        // form: the gathers of a group of kHH hops are issued before their
+        // multiply-adds, so each warp has that many requests in flight per
+        // memory latency (pays far from half filling, where x is in DRAM and
+        // a thread has one row); lean form: a plain unrolled loop (fewer
+        // instructions, which pays where the kernel is issue-bound).
+        constexpr int kHH = 16 / RR;
+        bool rv[RR];
+#pragma unroll
+        for (int i = 0; i < RR; ++i) rv[i] = tid + i * kThreads < nk;
+        if constexpr (!DEEP) {
+#pragma unroll 4
+            for (int j = 0; j < nhh; ++j) {
+                const T *xb = s.hp[j];
+                const A g = s.hg[j];
+#pragma unroll
+                for (int i = 0; i < RR; ++i)
+                    if (rv[i]) acc[i] += g * A(__ldg(xb + tid + i * kThreads));
+            }
+        }
+        for (int j0 = 0; DEEP && j0 < nhh; j0 += kHH) {
+            T v[kHH][RR];
+#pragma unroll
+            for (int u = 0; u < kHH; ++u) {
+                const bool ok = j0 + u < nhh;
+                const T *xb = s.hp[ok ? j0 + u : 0];
+#pragma unroll
+                for (int i = 0; i < RR; ++i) v[u][i] = (ok && rv[i]) ? __ldg(xb + tid + i * kThreads) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kHH; ++u) {
+                const A g = (j0 + u < nhh) ? s.hg[j0 + u] : A(0);
+#pragma unroll
+                for (int i = 0; i < RR; ++i) acc[i] += g * A(v[u][i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RR; ++i) {
+            if (tid + i * kThreads >= nk) continue;
+            const uint32_t l = lr[i];
+            A a = acc[i];
+            // high -> low: occupied high orbit P_a to empty low orbit e (block h - P_a)
+            if (k < L) {
+                uint32_t em = ~l & maskL;
+                for (int t = 0; t < L - k; ++t) {
+                    const int e = __ffs(em) - 1;
+                    em &= em - 1;
+                    const uint32_t off = s.rank[l | (1u << e)];
+                    const A *g = s.gs + e;
+                    if constexpr (!DEEP) {
+#pragma unroll 4
+                        for (int ai = 0; ai < ph; ++ai) a += g[ai * L] * A(__ldg(s.xo[ai] + off));
+                        continue;
+                    }
+                    for (int a0 = 0; a0 < ph; a0 += 8) {
+                        T v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            v[u] = (a0 + u < ph) ? __ldg(s.xo[a0 + u] + off) : T(0);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (a0 + u < ph) a += g[(a0 + u) * L] * A(v[u]);
+                    }
+                }
+            }
+            // low -> high: occupied low orbit o to empty high orbit q_c (block h + q_c)
+            if (k > 0) {
+                uint32_t oc = l;
+                for (int t = 0; t < k; ++t) {
+                    const int o = __ffs(oc) - 1;
+                    oc &= oc - 1;
+                    const uint32_t off = s.rank[l ^ (1u << o)];
+                    const A *g = s.ge + o;
+                    if constexpr (!DEEP) {
+#pragma unroll 4
+                        for (int c = 0; c < nemp; ++c) a += g[c * L] * A(__ldg(s.xe[c] + off));
+                        continue;
+                    }
+                    for (int c0 = 0; c0 < nemp; c0 += 8) {
+                        T v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            v[u] = (c0 + u < nemp) ? __ldg(s.xe[c0 + u] + off) : T(0);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (c0 + u < nemp) a += g[(c0 + u) * L] * A(v[u]);
+                    }
+                }
+            }
+            acc[i] = a;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RR; ++i) {
+        const int r = tid + i * kThreads;
+        if (r < nk) y[base + r] = T(acc[i]);
+    }
+    if (swdot) warp_dot<T, A, RR>(acc, s.x, nk, swdot);
+}
+
+// One basis block of y = H x in variant 3.  Called by every thread after a
+// barrier that frees the previous block's shared memory.
+template <typename T, typename A, int R, bool DEEP>
 __device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega, const int L, const int H,
                                           const int N, const uint64_t h, const uint64_t base,
                                           const uint16_t *__restrict__ lowword, const T *__restrict__ x,
                                           T *__restrict__ y, double *swdot)
 {
     const int tid = threadIdx.x;
-    const uint32_t maskL = (1u << L) - 1u;
     const int ph = __popcll(h);
     const int k = N - ph;
     const int nemp = H - ph;
@@ -874,141 +1097,35 @@ __device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega,
         const uint64_t *row = s.bin + q * NB;
         const uint64_t bb = (a1 <= b) ? SA - (s.sa[b] - s.sa[a1 - 1]) + (s.sb[b] - s.sb[a1]) + row[k + b]
                                       : SA - (s.sa[a1] - s.sa[b]) + (s.sc[a1 - 1] - s.sc[b]) + row[k + b + 1];
-        s.hh[t].base = bb;
-        s.hh[t].g = s.G[(L + q) * omega + (L + s.pos[a1 - 1])];
+        s.hp[t] = x + bb;
+        s.hg[t] = s.G[(L + q) * omega + (L + s.pos[a1 - 1])];
     }
-    for (int a = tid; a < ph; a += kThreads) s.mxo[a] = (k < L) ? s.sc[a] + SA - s.sa[a + 1] : 0ull;
+    for (int a = tid; a < ph; a += kThreads) s.xo[a] = x + ((k < L) ? s.sc[a] + SA - s.sa[a + 1] : 0ull);
     for (int c = tid; c < nemp; c += kThreads) {
         const int b = s.eb[c];
-        s.mxe[c] = (k > 0) ? s.sb[b] + s.bin[s.emp[c] * NB + k + b] + SA - s.sa[b] : 0ull;
+        s.xe[c] = x + ((k > 0) ? s.sb[b] + s.bin[s.emp[c] * NB + k + b] + SA - s.sa[b] : 0ull);
     }
-
-    A Dh = A(0);
-    for (uint64_t w = h; w; w &= w - 1) Dh += s.d[L + __ffsll((long long)w) - 1];
-
-    uint32_t lr[R];
-    A acc[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int r = tid + i * kThreads;
-        lr[i] = 0;
-        acc[i] = A(0);
-        if (r < nk) {
-            const uint32_t l = __ldg(lw + r);
-            lr[i] = l;
-            A D = A(0);
-            for (uint32_t w = l; w; w &= w - 1) D += s.d[__ffs(w) - 1];
-            acc[i] = (D + Dh) * A(s.x[r]);
-        }
+    for (int i = tid; i < ph * L; i += kThreads) {
+        const int a = i / L, e = i - a * L;
+        s.gs[i] = s.G[e * omega + L + s.pos[a]];
     }
-
-    // low -> low (own block, shared memory)
-    if (k > 0 && k < L) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            if (tid + i * kThreads < nk) {
-                const uint32_t l = lr[i];
-                A a = acc[i];
-                for (uint32_t oc = l; oc; oc &= oc - 1) {
-                    const int o = __ffs(oc) - 1;
-                    const uint32_t lo = l ^ (1u << o);
-                    const A *gcol = s.G + o;
-                    for (uint32_t em = ~l & maskL; em; em &= em - 1) {
-                        const int q = __ffs(em) - 1;
-                        a += gcol[q * omega] * A(s.x[s.rank[lo | (1u << q)]]);
-                    }
-                }
-                acc[i] = a;
-            }
-        }
+    for (int i = tid; i < nemp * L; i += kThreads) {
+        const int c = i / L, o = i - c * L;
+        s.ge[i] = s.G[(L + s.emp[c]) * omega + o];
     }
     __syncthreads();                              // hop tables visible
-
-    // The gathers below go to L2 or DRAM.  Each group issues kU independent
-    // loads before the multiply-adds that consume them, so a warp keeps kU
-    // requests in flight instead of waiting a full memory latency per hop.
-    constexpr int kU = (R >= 4) ? 4 : 8;
-    // high -> high: same offsets in the target block (coalesced)
-    for (int j0 = 0; j0 < nhh; j0 += kU) {
-        T v[kU][R];
-        A g[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int j = j0 + u;
-            const bool ok = j < nhh;
-            const T *xb = x + (ok ? s.hh[j].base : 0ull);
-            g[u] = ok ? s.hh[j].g : A(0);
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = tid + i * kThreads;
-                v[u][i] = (ok && r < nk) ? __ldg(xb + r) : T(0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-#pragma unroll
-            for (int i = 0; i < R; ++i) acc[i] += g[u] * A(v[u][i]);
-    }
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        if (tid + i * kThreads >= nk) continue;
-        const uint32_t l = lr[i];
-        A a = acc[i];
-        // high -> low: occupied high orbit P_a to empty low orbit e (block h - P_a)
-        if (k < L) {
-            for (uint32_t em = ~l & maskL; em; em &= em - 1) {
-                const int e = __ffs(em) - 1;
-                const uint64_t off = s.rank[l | (1u << e)];
-                const A *grow = s.G + e * omega + L;
-                for (int a0 = 0; a0 < ph; a0 += kU) {
-                    T v[kU];
-                    A g[kU];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const int aa = a0 + u;
-                        const bool ok = aa < ph;
-                        v[u] = ok ? __ldg(x + s.mxo[aa] + off) : T(0);
-                        g[u] = ok ? grow[s.pos[aa]] : A(0);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) a += g[u] * A(v[u]);
-                }
-            }
-        }
-        // low -> high: occupied low orbit o to empty high orbit q (block h + q)
-        if (k > 0) {
-            for (uint32_t oc = l; oc; oc &= oc - 1) {
-                const int o = __ffs(oc) - 1;
-                const uint64_t off = s.rank[l ^ (1u << o)];
-                const A *gcol = s.G + L * omega + o;
-                for (int c0 = 0; c0 < nemp; c0 += kU) {
-                    T v[kU];
-                    A g[kU];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const int c = c0 + u;
-                        const bool ok = c < nemp;
-                        v[u] = ok ? __ldg(x + s.mxe[c] + off) : T(0);
-                        g[u] = ok ? gcol[s.emp[c] * omega] : A(0);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) a += g[u] * A(v[u]);
-                }
-            }
-        }
-        acc[i] = a;
-    }
-
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int r = tid + i * kThreads;
-        if (r < nk) y[base + r] = T(acc[i]);
-    }
-    if (swdot) warp_dot<T, A, R>(acc, s.x, nk, swdot);
+    // the row work, unrolled for the rows per thread this block needs
+    const int rpt = (nk + kThreads - 1) / kThreads;
+    if (rpt <= 1) hx3_rows<T, A, 1, DEEP>(s, omega, L, h, base, lw, y, swdot, k, ph, nemp, nhh, nk);
+    else if (rpt <= 2)
+        hx3_rows<T, A, (R < 2 ? R : 2), DEEP>(s, omega, L, h, base, lw, y, swdot, k, ph, nemp, nhh, nk);
+    else if (rpt <= 4)
+        hx3_rows<T, A, (R < 4 ? R : 4), DEEP>(s, omega, L, h, base, lw, y, swdot, k, ph, nemp, nhh, nk);
+    else hx3_rows<T, A, R, DEEP>(s, omega, L, h, base, lw, y, swdot, k, ph, nemp, nhh, nk);
 }
 
-template <typename T, typename A, int R>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, typename A, int R, bool DEEP>
+__global__ void __launch_bounds__(kThreads, 4)
 hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, const T *__restrict__ x,
            T *__restrict__ y, Tickets *tk, const int *__restrict__ skip, double *blk_part, double *dot_out)
 {
@@ -1038,7 +1155,7 @@ hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, c
             if (b < B.nblocks) s_next[it ^ 1] = (long long)atomicAdd(&tk->hx_next, 1ull);
         }
         if (b >= B.nblocks) break;
-        hx3_block<T, A, R>(s, omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, x, y,
+        hx3_block<T, A, R, DEEP>(s, omega, L, H, N, __ldg(B.blk_h + b), __ldg(B.blk_base + b), B.lowword, x, y,
                            blk_part ? swdot : nullptr);
         prev = b;
     }
@@ -1057,11 +1174,12 @@ bool use_v2(const Blocks &B)
     return layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total <= kSmemLimit;
 }
 
-// Variant 3 on request, when its shared memory fits (full space only)
+// Variant 3 (lean loops) or 4 (deep gather groups) on request, when the shared
+// memory fits (full space only)
 template <typename T, typename A>
 bool use_v3(const Blocks &B)
 {
-    if (B.variant != 3 || B.kept_map) return false;
+    if ((B.variant != 3 && B.variant != 4) || B.kept_map) return false;
     return layout3<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total <= kSmemLimit;
 }
 
@@ -1069,7 +1187,8 @@ template <typename T, typename A, int R>
 const void *kernel_fn(const Blocks &B)
 {
     if (B.kept_map) return (const void *)hx_kernel<T, A, R, true>;
-    if (use_v3<T, A>(B)) return (const void *)hx3_kernel<T, A, R>;
+    if (use_v3<T, A>(B))
+        return B.variant == 4 ? (const void *)hx3_kernel<T, A, R, true> : (const void *)hx3_kernel<T, A, R, false>;
     return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R, false>;
 }
 
@@ -1095,9 +1214,12 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     if (B.kept_map)
         hx_kernel<T, A, R, true><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                                static_cast<T *>(y), tk, skip, bp, out);
+    else if (use_v3<T, A>(B) && B.variant == 4)
+        hx3_kernel<T, A, R, true><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                                static_cast<T *>(y), tk, skip, bp, out);
     else if (use_v3<T, A>(B))
-        hx3_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
-                                                          static_cast<T *>(y), tk, skip, bp, out);
+        hx3_kernel<T, A, R, false><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                                 static_cast<T *>(y), tk, skip, bp, out);
     else if (v2)
         hx2_kernel<T, A, R><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                           static_cast<T *>(y), tk, skip, bp, out);
@@ -1136,7 +1258,8 @@ int grid_prec(const Blocks &B)
         per_sm < 1)
         per_sm = 1;
     int64_t g = (int64_t)sms * per_sm;
-    if (g > B.nblocks) g = B.nblocks;
+    const int64_t nbk = B.kept_map ? B.kept_nblocks : B.nblocks;   // blocks a launch walks
+    if (g > nbk) g = nbk;
     return (int)(g > 0 ? g : 1);
 }
 
@@ -1343,7 +1466,7 @@ size_t hx_smem_bytes(const Blocks &B, int precision)
 
 int hx_variant(const Blocks &B, int precision)
 {
-    if (precision == 0 ? use_v3<double, double>(B) : use_v3<float, float>(B)) return 3;
+    if (precision == 0 ? use_v3<double, double>(B) : use_v3<float, float>(B)) return B.variant;
     return (precision == 0 ? use_v2<double, double>(B) : use_v2<float, float>(B)) ? 2 : 1;
 }
 

@@ -22,6 +22,9 @@ namespace pd {
 // ---- host helpers (pd_api.cu) ------------------------------------------------
 // record a one-line error for pairdiag_last_error() and return `code`
 int fail(int code, const char *fmt, ...);
+// streaming multiprocessors of the current device (looked up once per device)
+int sm_count();
+constexpr int kMaxDevices = 64;      // device ordinals the per-device caches cover
 uint64_t host_binom(int n, int m);                        // Pascal table, 0 outside 0 <= m <= n <= 63
 uint64_t host_block_base(uint64_t hw, int L, int N);      // index of the block with high word hw
 void words_with_popcount(int bits, int c, std::vector<uint64_t> &out);   // ascending
@@ -88,6 +91,9 @@ struct Blocks {
     // kept states, -1 for a dropped state; nullptr = the full space.  Vectors of
     // a truncated handle hold the kept states only, in basis order.
     const int32_t *kept_map;
+    // the blocks holding at least one kept state (the truncated H*x walks only these)
+    const uint64_t *kept_blk_h, *kept_blk_base;
+    int64_t kept_nblocks;
 };
 
 // ---- many problems at once (batched solver) ---------------------------------
@@ -339,7 +345,10 @@ struct LanczosScalars {              // lives in device memory
     int    used;                     // valid Lanczos steps of the current cycle
     int    broken;                   // breakdown seen: later steps of the cycle are skipped
 };
-int vec_grid();                      // CTAs of the streaming vector kernels
+// CTAs of the streaming vector kernels on the current device: 4 per SM, at
+// most kMaxVecGrid (the partial-sum buffers hold kMaxVecGrid rows)
+constexpr int kMaxVecGrid = 1024;
+int vec_grid();
 // Streaming kernels: vectors of n elements; Q holds vectors j at Q + j*ld.  They
 // move 16-byte packs when every vector is 16-byte aligned (ld a multiple of the
 // pack), else single elements.  partials: [vec_grid() * kMaxWindow] doubles.

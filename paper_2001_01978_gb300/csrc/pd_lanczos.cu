@@ -18,7 +18,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kGroup = 8;             // vectors handled per pass of a multi-vector kernel
-constexpr int kGrid = 152 * 4;
+// at most 4 CTAs per SM for the streaming kernels, and no more than the
+// partial-sum buffers hold
+inline int grid_cap()
+{
+    const int g = sm_count() * 4;
+    return g < kMaxVecGrid ? g : kMaxVecGrid;
+}
 
 template <typename T>
 __device__ __forceinline__ T fma_t(T a, T b, T c);
@@ -991,7 +997,8 @@ __global__ void batch_rayleigh_kernel(BatchState *S, int count, int stage)
 
 int seg_grid(const BatchVec &V)
 {
-    int g = V.nchunks < 152 * 8 ? V.nchunks : 152 * 8;
+    const int cap = sm_count() * 8;
+    int g = V.nchunks < cap ? V.nchunks : cap;
     return g > 0 ? g : 1;
 }
 
@@ -1008,7 +1015,7 @@ inline void seg_reduce(const BatchVec &V, int m, const BatchState *S, int use_sk
 int grid_for(int64_t n)
 {
     int64_t g = (n + kThreads - 1) / kThreads;
-    if (g > kGrid) g = kGrid;
+    if (g > grid_cap()) g = grid_cap();
     return (int)(g > 0 ? g : 1);
 }
 
@@ -1025,21 +1032,27 @@ bool packable(std::initializer_list<const void *> ptrs, int64_t ld)
 }
 
 // CTAs of one wave of a streaming kernel: SMs x resident CTAs per SM (looked up
-// once per kernel), at most kGrid, and no more than the work needs
+// once per kernel and device), at most grid_cap(), and no more than the work needs
 template <auto kernel>
 int wave_grid(int64_t units)
 {
-    static const int wave = [] {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    int wave = cache[dev].load(std::memory_order_relaxed);
+    if (wave <= 0) {
+        int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) {
             cudaGetLastError();
             per_sm = 1;
         }
-        const int w = sms * (per_sm > 0 ? per_sm : 1);
-        return w < kGrid ? w : kGrid;
-    }();
+        const int w = sm_count() * (per_sm > 0 ? per_sm : 1);
+        wave = w < grid_cap() ? w : grid_cap();
+        cache[dev].store(wave, std::memory_order_relaxed);
+    }
     const int g = grid_for(units);
     return g < wave ? g : wave;
 }
@@ -1119,7 +1132,7 @@ void ritz_t(T *Q, int64_t ld, const int *m_dev, const double *s, int64_t n, doub
 
 }  // namespace
 
-int vec_grid() { return kGrid; }
+int vec_grid() { return grid_cap(); }
 
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
                             double *partials, double *out, cudaStream_t st, const int *skip,

@@ -8,9 +8,10 @@
 // problem, w* minimises sum_s psi(s)^2 (log|psi(s)| - sum_{i in s} w_i)^2.
 //
 // Network: 16 -> 128 -> 128 -> 128 -> 1, SiLU, bfloat16 operands with FP32
-// accumulation on the tensor cores (mma.sync m16n8k16), FP32 master weights,
-// Adam.  Sizes are tiny (rows = orbits of the training problems), so one tiled
-// kernel serves every product of the forward and backward passes.
+// accumulation on the tensor cores (tcgen05.mma, accumulators in tensor
+// memory), FP32 master weights, Adam.  Sizes are tiny (rows = orbits of the
+// training problems), so one tiled kernel serves every product of the forward
+// and backward passes.
 #include "pd_internal.h"
 #include "pairdiag.h"
 
@@ -31,95 +32,195 @@ constexpr int oW1 = 0, ob1 = oW1 + kF * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
 
 using bf16 = __nv_bfloat16;
 
-// ---- C[M,N] (+)= op(A)[M,K] op(B)[K,N], bfloat16 operands, FP32 accumulation --
+// ---- C[M,128] (=, or += over split K) op(A)[M,K] op(B)[K,128] on the 5th-generation
+// tensor cores: tcgen05.mma with bfloat16 operands in shared memory and an FP32
+// accumulator in tensor memory (TMEM).
 // A(m,k) = TA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n].
-// 64x64 tile per CTA (4 warps of 32x32), K split over gridDim.z with atomic adds.
-constexpr int kTM = 64, kTN = 64, kBK = 16, kPad = 8;
+// Every product of the network has N = 128 (the layer width).  One CTA of 128
+// threads computes a 128 x 128 tile of C over a range of K (split K over
+// gridDim.y, added with atomics into a zeroed C):
+//   - the four warps stage a 128 x 64 slice of A and of B^T in shared memory in
+//     the canonical K-major layout without swizzle: 8 x 16-byte core matrices,
+//     element (r, k) at (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+//     bytes, so the leading (K) byte offset of the descriptor is 128 and the
+//     stride (8-row) byte offset 1024;
+//   - one thread issues four tcgen05.mma (M = N = 128, K = 16 each) into the
+//     TMEM accumulator (128 lanes = rows of C, 128 columns) and commits them
+//     to an mbarrier, which every thread waits on before the slice is
+//     overwritten;
+//   - the epilogue reads the accumulator with tcgen05.ld (each warp its 32
+//     lanes) and writes C.
+// Waits are bounded: on expiry the kernel sets *err, still frees its TMEM and
+// returns (the caller reports PD_ETIMEOUT).  The network's products are tiny
+// (M = the orbit rows of the problems, K <= rows), so staging by threads
+// instead of TMA is no bottleneck.
+constexpr int kTileM = 128, kTileN = 128, kSliceK = 64;
+constexpr int kTmemCols = 128;                 // one FP32 column per output column
+constexpr long long kSpinLimit = 1ll << 26;    // mbarrier polls before giving up
+constexpr int kGemmPadSmem = 18 * 1024;
 
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                 "{%8,%9}, {%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);            // start address
+    d |= (uint64_t)((128u & 0x3FFFFu) >> 4) << 16;        // leading (K) byte offset: next core matrix in K
+    d |= (uint64_t)((1024u & 0x3FFFFu) >> 4) << 32;       // stride byte offset: next 8 rows
+    d |= (uint64_t)1 << 46;                               // descriptor version of this architecture
+    return d;                                             // base offset 0, no swizzle
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128, M = 128
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                                ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+{
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(phase)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// stage rows [r0, r0 + 128) x k [k0, k0 + 64) of op(X) (row index r, column k)
+// into the canonical layout; zero outside [0, nrow) x [k0, kend)
+template <bool TR>
+__device__ __forceinline__ void stage_slice(unsigned char *dst, const bf16 *__restrict__ X, int ld, int r0, int nrow,
+                                            int k0, int kend)
+{
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (int it = threadIdx.x; it < kTileM * (kSliceK / 8); it += blockDim.x) {
+        const int r = it % kTileM, kc = it / kTileM;        // consecutive threads: consecutive rows
+        const int gr = r0 + r;
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gk = k0 + kc * 8 + j;
+            v[j] = (gr < nrow && gk < kend) ? (TR ? X[(size_t)gk * ld + gr] : X[(size_t)gr * ld + gk]) : zero;
+        }
+        *reinterpret_cast<uint4 *>(dst + (r >> 3) * 1024 + kc * 128 + (r & 7) * 16) =
+            *reinterpret_cast<const uint4 *>(v);
+    }
 }
 
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128)
-gemm_kernel(int M, int N, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
-            float *__restrict__ C, int ldc, int accumulate)
+gemm_tc_kernel(int M, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
+               float *__restrict__ C, int ldc, int *err)
 {
-    __shared__ __align__(16) bf16 As[kTM][kBK + kPad];
-    __shared__ __align__(16) bf16 Bs[kTN][kBK + kPad];
-    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-    const int kchunk = ((K + gridDim.z - 1) / gridDim.z + kBK - 1) / kBK * kBK;
-    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    __shared__ __align__(1024) unsigned char sA[kTileM * kSliceK * 2];
+    __shared__ __align__(1024) unsigned char sB[kTileN * kSliceK * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
-    const bf16 zero = __float2bfloat16(0.0f);
-    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
-        for (int idx = tid; idx < kTM * kBK; idx += 128) {
-            const int m = idx / kBK, k = idx % kBK, gm = m0 + m, gk = k0 + k;
-            As[m][k] = (gm < M && gk < kend) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : zero;
-        }
-        for (int idx = tid; idx < kTN * kBK; idx += 128) {
-            const int n = idx / kBK, k = idx % kBK, gn = n0 + n, gk = k0 + k;
-            Bs[n][k] = (gn < N && gk < kend) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : zero;
-        }
-        __syncthreads();
-        uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = wm + i * 16 + g;
-            af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][tq * 2]);
-            af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][tq * 2]);
-            af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][tq * 2 + 8]);
-            af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][tq * 2 + 8]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = wn + j * 8 + g;
-            bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][tq * 2]);
-            bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][tq * 2 + 8]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
-        __syncthreads();
+    const int m0 = blockIdx.x * kTileM;
+    const int kchunk = ((K + gridDim.y - 1) / gridDim.y + kSliceK - 1) / kSliceK * kSliceK;
+    const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
+    if (kbeg >= kend) return;                          // CTA-uniform: nothing to add
+    const bool split = gridDim.y > 1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    const bool atomic = gridDim.z > 1;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB), barp = smem_u32(&bar);
+
+    uint32_t phase = 0;
+    bool timed_out = false;
+    for (int k0 = kbeg; k0 < kend && !timed_out; k0 += kSliceK) {
+        stage_slice<TA>(sA, A, lda, m0, M, k0, kend);
+        stage_slice<!TB>(sB, B, ldb, 0, kTileN, k0, kend);   // row n of B^T: B(k, n)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // generic-proxy stores -> async proxy
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int sk = 0; sk < kSliceK / 16; ++sk) {
+                const uint64_t da = umma_desc(a0 + sk * 256), db = umma_desc(b0 + sk * 256);
+                const uint32_t accum = (k0 == kbeg && sk == 0) ? 0u : 1u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                             "l"(da), "l"(db), "r"(kIdescBf16), "r"(accum)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barp)
+                         : "memory");
+        }
+        // the slice may be overwritten only after these MMAs have read it
+        const bool ok = mbar_wait(barp, phase);
+        phase ^= 1u;
+        timed_out = __syncthreads_or(!ok) != 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+                         "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+                         "%28, %29, %30, %31}, [%32];\n"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                         : "r"(taddr)
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < M) {
+                float *dst = C + (size_t)row * ldc + c0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int r = m0 + wm + i * 16 + g + (c >= 2 ? 8 : 0);
-                const int col = n0 + wn + j * 8 + tq * 2 + (c & 1);
-                if (r < M && col < N) {
-                    float *dst = C + (size_t)r * ldc + col;
-                    if (atomic) atomicAdd(dst, acc[i][j][c]);
-                    else *dst = accumulate ? *dst + acc[i][j][c] : acc[i][j][c];
+                for (int j = 0; j < 32; ++j) {
+                    const float f = __uint_as_float(v[j]);
+                    if (split) atomicAdd(dst + j, f);
+                    else dst[j] = f;
                 }
             }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// C[M, 128] = op(A) op(B) (split K over ksplit CTAs per row tile, C zeroed first)
 template <bool TA, bool TB>
 void gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, float *C, int ldc, int ksplit,
-          cudaStream_t st)
+          int *err, cudaStream_t st)
 {
-    dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, ksplit);
+    (void)N;                                   // always kTileN (the layer width)
+    dim3 grid((M + kTileM - 1) / kTileM, ksplit);
     if (ksplit > 1) cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * ldc, st);
-    gemm_kernel<TA, TB><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, 0);
+    // 18 KB of unused dynamic shared memory keep at most four CTAs on an SM,
+    // so their 4 x 128 TMEM columns fit the SM's 512 and no allocation waits
+    static const cudaError_t attr =       // static + dynamic shared memory above 48 KB needs the opt-in
+        cudaFuncSetAttribute(gemm_tc_kernel<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmPadSmem);
+    (void)attr;
+    gemm_tc_kernel<TA, TB><<<grid, 128, kGemmPadSmem, st>>>(M, K, A, lda, B, ldb, C, ldc, err);
     count_launches(1);
 }
 
@@ -239,8 +340,11 @@ struct pairdiag_mlp {
     bf16 *wb = nullptr;          // bfloat16 copies (same layout)
     float *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
     int cap = 0;                 // rows the work buffers hold
-    bf16 *X = nullptr, *A1 = nullptr, *A2 = nullptr, *A3 = nullptr, *dZ = nullptr;
-    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dA = nullptr, *out = nullptr, *t = nullptr, *dout = nullptr;
+    bf16 *X = nullptr, *A1 = nullptr, *A2 = nullptr, *A3 = nullptr;
+    bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr;   // backward intermediates, one per layer
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dA1 = nullptr, *dA2 = nullptr;
+    float *out = nullptr, *t = nullptr, *dout = nullptr;
+    int *err = nullptr;          // set by a tensor-core product whose bounded wait expired
     double *loss = nullptr;
     int steps = 0;
     cudaStream_t st = nullptr;
@@ -250,11 +354,12 @@ namespace {
 
 void mlp_free_work(pairdiag_mlp *m)
 {
-    void *p[] = {m->X, m->A1, m->A2, m->A3, m->dZ, m->Z1, m->Z2, m->Z3, m->dA, m->out, m->t, m->dout};
+    void *p[] = {m->X, m->A1, m->A2, m->A3, m->dZ1, m->dZ2, m->dZ3, m->Z1, m->Z2, m->Z3, m->dA1, m->dA2,
+                 m->out, m->t, m->dout};
     for (void *q : p)
         if (q) cudaFree(q);
-    m->X = m->A1 = m->A2 = m->A3 = m->dZ = nullptr;
-    m->Z1 = m->Z2 = m->Z3 = m->dA = m->out = m->t = m->dout = nullptr;
+    m->X = m->A1 = m->A2 = m->A3 = m->dZ1 = m->dZ2 = m->dZ3 = nullptr;
+    m->Z1 = m->Z2 = m->Z3 = m->dA1 = m->dA2 = m->out = m->t = m->dout = nullptr;
     m->cap = 0;
 }
 
@@ -267,11 +372,14 @@ int mlp_reserve(pairdiag_mlp *m, int rows)
     PD_CUDA(cudaMalloc(&m->A1, sizeof(bf16) * nh));
     PD_CUDA(cudaMalloc(&m->A2, sizeof(bf16) * nh));
     PD_CUDA(cudaMalloc(&m->A3, sizeof(bf16) * nh));
-    PD_CUDA(cudaMalloc(&m->dZ, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->dZ1, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->dZ2, sizeof(bf16) * nh));
+    PD_CUDA(cudaMalloc(&m->dZ3, sizeof(bf16) * nh));
     PD_CUDA(cudaMalloc(&m->Z1, sizeof(float) * nh));
     PD_CUDA(cudaMalloc(&m->Z2, sizeof(float) * nh));
     PD_CUDA(cudaMalloc(&m->Z3, sizeof(float) * nh));
-    PD_CUDA(cudaMalloc(&m->dA, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->dA1, sizeof(float) * nh));
+    PD_CUDA(cudaMalloc(&m->dA2, sizeof(float) * nh));
     PD_CUDA(cudaMalloc(&m->out, sizeof(float) * rows));
     PD_CUDA(cudaMalloc(&m->t, sizeof(float) * rows));
     PD_CUDA(cudaMalloc(&m->dout, sizeof(float) * rows));
@@ -279,18 +387,31 @@ int mlp_reserve(pairdiag_mlp *m, int rows)
     return PD_OK;
 }
 
-int grid1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+int grid1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8)); }
+
+// after a synchronisation of m->st: PD_ETIMEOUT (and the flag cleared) when a
+// tensor-core product gave up waiting for its MMAs
+int check_tc(pairdiag_mlp *m)
+{
+    int e = 0;
+    PD_CUDA(cudaMemcpy(&e, m->err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        PD_CUDA(cudaMemset(m->err, 0, sizeof e));
+        return fail(PD_ETIMEOUT, "mlp: a tensor-core product timed out waiting for its MMAs");
+    }
+    return PD_OK;
+}
 
 // forward pass on m->X (rows x 16, bfloat16) -> m->out
 int mlp_forward(pairdiag_mlp *m, int rows)
 {
     cudaStream_t st = m->st;
     to_bf16_kernel<<<grid1(kNParams), 256, 0, st>>>(m->theta, m->wb, kNParams);
-    gemm<false, false>(rows, kH, kF, m->X, kF, m->wb + oW1, kH, m->Z1, kH, 1, st);
+    gemm<false, false>(rows, kH, kF, m->X, kF, m->wb + oW1, kH, m->Z1, kH, 1, m->err, st);
     bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z1, m->theta + ob1, m->A1, rows);
-    gemm<false, false>(rows, kH, kH, m->A1, kH, m->wb + oW2, kH, m->Z2, kH, 1, st);
+    gemm<false, false>(rows, kH, kH, m->A1, kH, m->wb + oW2, kH, m->Z2, kH, 1, m->err, st);
     bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z2, m->theta + ob2, m->A2, rows);
-    gemm<false, false>(rows, kH, kH, m->A2, kH, m->wb + oW3, kH, m->Z3, kH, 1, st);
+    gemm<false, false>(rows, kH, kH, m->A2, kH, m->wb + oW3, kH, m->Z3, kH, 1, m->err, st);
     bias_silu_kernel<<<grid1((int64_t)rows * kH), 256, 0, st>>>(m->Z3, m->theta + ob3, m->A3, rows);
     head_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(m->A3, m->wb + ow4, m->theta + ob4, m->out, rows);
     count_launches(5);
@@ -308,17 +429,17 @@ int mlp_backward(pairdiag_mlp *m, int rows)
     loss_kernel<<<std::max(1, std::min(64, (rows + 255) / 256)), 256, 0, st>>>(m->out, m->t, m->dout, rows, m->loss);
     const int gr = std::max(1, std::min(1024, rows));
     head_back_kernel<<<gr, kH, 0, st>>>(m->A3, m->Z3, m->wb + ow4, m->dout, rows, m->grad + ow4, m->grad + ob4,
-                                        m->dZ, m->grad + ob3);
+                                        m->dZ3, m->grad + ob3);
     // layer 3: gW3 = A2^T dZ3 (written straight into the gradient), dA2 = dZ3 W3^T
-    gemm<true, false>(kH, kH, rows, m->A2, kH, m->dZ, kH, m->grad + oW3, kH, ks, st);
-    gemm<false, true>(rows, kH, kH, m->dZ, kH, m->wb + oW3, kH, m->dA, kH, 1, st);
-    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA, m->Z2, rows, m->dZ, m->grad + ob2);
+    gemm<true, false>(kH, kH, rows, m->A2, kH, m->dZ3, kH, m->grad + oW3, kH, ks, m->err, st);
+    gemm<false, true>(rows, kH, kH, m->dZ3, kH, m->wb + oW3, kH, m->dA2, kH, 1, m->err, st);
+    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA2, m->Z2, rows, m->dZ2, m->grad + ob2);
     // layer 2
-    gemm<true, false>(kH, kH, rows, m->A1, kH, m->dZ, kH, m->grad + oW2, kH, ks, st);
-    gemm<false, true>(rows, kH, kH, m->dZ, kH, m->wb + oW2, kH, m->dA, kH, 1, st);
-    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA, m->Z1, rows, m->dZ, m->grad + ob1);
+    gemm<true, false>(kH, kH, rows, m->A1, kH, m->dZ2, kH, m->grad + oW2, kH, ks, m->err, st);
+    gemm<false, true>(rows, kH, kH, m->dZ2, kH, m->wb + oW2, kH, m->dA1, kH, 1, m->err, st);
+    dsilu_kernel<<<gr, kH, 0, st>>>(m->dA1, m->Z1, rows, m->dZ1, m->grad + ob1);
     // layer 1: gW1 = X^T dZ1
-    gemm<true, false>(kF, kH, rows, m->X, kF, m->dZ, kH, m->grad + oW1, kH, ks, st);
+    gemm<true, false>(kF, kH, rows, m->X, kF, m->dZ1, kH, m->grad + oW1, kH, ks, m->err, st);
     count_launches(4);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
@@ -337,12 +458,16 @@ int mlp_load_inputs(pairdiag_mlp *m, int rows, const float *X, const float *t)
 
 // ---- start vector and target fit over the basis blocks ---------------------------
 // v[s] = exp(sum_{p in s} w_p - shift)
+struct OrbitWeights {                   // per-orbit weights, passed by value (no device allocation)
+    double w[kMaxOmega];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-product_start_kernel(const Blocks B, const double *__restrict__ w, double shift, T *__restrict__ v)
+product_start_kernel(const Blocks B, const OrbitWeights w, double shift, T *__restrict__ v)
 {
     __shared__ double sw[kMaxOmega];
-    for (int p = threadIdx.x; p < B.omega; p += blockDim.x) sw[p] = w[p];
+    for (int p = threadIdx.x; p < B.omega; p += blockDim.x) sw[p] = w.w[p];
     __syncthreads();
     for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
         const uint64_t h = B.blk_h[b], base = B.blk_base[b];
@@ -459,6 +584,7 @@ int batch_mlp_start(struct ::pairdiag_mlp *m, const BatchBlocks &BB, int count, 
     std::vector<float> o(rows);
     PD_CUDA(cudaMemcpyAsync(o.data(), m->out, sizeof(float) * rows, cudaMemcpyDeviceToHost, m->st));
     PD_CUDA(cudaStreamSynchronize(m->st));
+    PD_TRY(check_tc(m));
     std::vector<double> w(o.begin(), o.end()), shift(count);
     for (int p = 0; p < count; ++p) {
         std::vector<double> srt(w.begin() + woff[p], w.begin() + woff[p] + omega[p]);
@@ -476,7 +602,7 @@ int batch_mlp_start(struct ::pairdiag_mlp *m, const BatchBlocks &BB, int count, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(dsh, shift.data(), sizeof(double) * count, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dwo, woff.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(BB.nblocks, 152 * 8));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(BB.nblocks, sm_count() * 8));
         if (dtype == 0) batch_product_start_kernel<double><<<grid, 256, 0, st>>>(BB, dw, dwo, dsh, (double *)v);
         else batch_product_start_kernel<float><<<grid, 256, 0, st>>>(BB, dw, dwo, dsh, (float *)v);
         count_launches(1);
@@ -546,19 +672,14 @@ int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cud
     std::sort(srt.begin(), srt.end(), std::greater<double>());
     double shift = 0.0;
     for (int i = 0; i < B.n; ++i) shift += srt[i];        // the largest exponent over the basis
-    double *dw = nullptr;
-    PD_CUDA(cudaMalloc(&dw, sizeof(double) * B.omega));
-    cudaError_t e = cudaMemcpyAsync(dw, w.data(), sizeof(double) * B.omega, cudaMemcpyHostToDevice, st);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, 152 * 4));
-    if (e == cudaSuccess) {
-        if (dtype == 0) product_start_kernel<double><<<grid, 256, 0, st>>>(B, dw, shift, (double *)v);
-        else product_start_kernel<float><<<grid, 256, 0, st>>>(B, dw, shift, (float *)v);
-        count_launches(1);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(dw);
-    PD_CUDA(e);
+    OrbitWeights ow{};
+    for (int p = 0; p < B.omega; ++p) ow.w[p] = w[p];
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, sm_count() * 4));
+    if (dtype == 0) product_start_kernel<double><<<grid, 256, 0, st>>>(B, ow, shift, (double *)v);
+    else product_start_kernel<float><<<grid, 256, 0, st>>>(B, ow, shift, (float *)v);
+    count_launches(1);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaStreamSynchronize(st));
     return PD_OK;
 }
 
@@ -566,7 +687,7 @@ int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cud
 int product_fit(const Blocks &B, const double *v, double *w_out, cudaStream_t st)
 {
     const int om = B.omega, nacc = om * om + om;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, 152 * 2));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, sm_count() * 2));
     double *part = nullptr, *sum = nullptr;
     PD_CUDA(cudaMalloc(&part, sizeof(double) * (size_t)grid * nacc));
     cudaError_t e = cudaMalloc(&sum, sizeof(double) * nacc);
@@ -628,6 +749,7 @@ int mlp_predict(pairdiag_mlp *m, int omega, int n, const double *e, const double
     std::vector<float> o(omega);
     PD_CUDA(cudaMemcpyAsync(o.data(), m->out, sizeof(float) * omega, cudaMemcpyDeviceToHost, m->st));
     PD_CUDA(cudaStreamSynchronize(m->st));
+    PD_TRY(check_tc(m));
     for (int i = 0; i < omega; ++i) w_out[i] = o[i];
     return PD_OK;
 }
@@ -664,14 +786,15 @@ int pairdiag_mlp_create(uint64_t seed, pairdiag_mlp_t **out)
             cudaMalloc(&m->grad, sizeof(float) * kNParams) != cudaSuccess ||
             cudaMalloc(&m->m1, sizeof(float) * kNParams) != cudaSuccess ||
             cudaMalloc(&m->m2, sizeof(float) * kNParams) != cudaSuccess ||
-            cudaMalloc(&m->loss, sizeof(double)) != cudaSuccess) {
+            cudaMalloc(&m->loss, sizeof(double)) != cudaSuccess || cudaMalloc(&m->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             st = fail(PD_ENOMEM, "mlp: allocation failed");
             break;
         }
         if (cudaMemcpy(m->theta, th.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(m->m1, 0, sizeof(float) * kNParams) != cudaSuccess ||
-            cudaMemset(m->m2, 0, sizeof(float) * kNParams) != cudaSuccess)
+            cudaMemset(m->m2, 0, sizeof(float) * kNParams) != cudaSuccess ||
+            cudaMemset(m->err, 0, sizeof(int)) != cudaSuccess)
             st = fail(PD_ECUDA, "mlp: initialisation failed");
     } while (0);
     if (st != PD_OK) {
@@ -687,7 +810,7 @@ void pairdiag_mlp_destroy(pairdiag_mlp_t *m)
     if (!m) return;
     cudaStreamSynchronize(m->st);
     mlp_free_work(m);
-    void *p[] = {m->theta, m->wb, m->grad, m->m1, m->m2, m->loss};
+    void *p[] = {m->theta, m->wb, m->grad, m->m1, m->m2, m->loss, m->err};
     for (void *q : p)
         if (q) cudaFree(q);
     delete m;
@@ -727,7 +850,7 @@ int pairdiag_mlp_forward(pairdiag_mlp_t *m, int rows, const float *X, float *out
     PD_TRY(mlp_forward(m, rows));
     PD_CUDA(cudaMemcpyAsync(out, m->out, sizeof(float) * rows, cudaMemcpyDeviceToHost, m->st));
     PD_CUDA(cudaStreamSynchronize(m->st));
-    return PD_OK;
+    return check_tc(m);
 }
 
 int pairdiag_mlp_loss_grad(pairdiag_mlp_t *m, int rows, const float *X, const float *target, double *loss,
@@ -740,7 +863,7 @@ int pairdiag_mlp_loss_grad(pairdiag_mlp_t *m, int rows, const float *X, const fl
     PD_CUDA(cudaMemcpyAsync(grad, m->grad, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, m->st));
     PD_CUDA(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     PD_CUDA(cudaStreamSynchronize(m->st));
-    return PD_OK;
+    return check_tc(m);
 }
 
 int pairdiag_mlp_train(pairdiag_mlp_t *m, int rows, const float *X, const float *target, int steps, double lr,
@@ -771,6 +894,41 @@ int pairdiag_mlp_train(pairdiag_mlp_t *m, int rows, const float *X, const float 
     if (d_hist) cudaFree(d_hist);
     if (rc != PD_OK) return rc;
     PD_CUDA(e);
+    return check_tc(m);
+}
+
+int pairdiag_mlp_buffer(const pairdiag_mlp_t *m, int which, int rows, float *out)
+{
+    if (!m || !out || rows < 1) return fail(PD_EINVAL, "bad argument");
+    if (rows > m->cap) return fail(PD_EINVAL, "rows=%d beyond the last pass (%d rows)", rows, m->cap);
+    const size_t nh = (size_t)rows * kH;
+    const float *f = nullptr;
+    const bf16 *b = nullptr;
+    size_t n = nh;
+    switch (which) {
+    case PD_MLP_Z1: f = m->Z1; break;
+    case PD_MLP_A1: b = m->A1; break;
+    case PD_MLP_Z2: f = m->Z2; break;
+    case PD_MLP_A2: b = m->A2; break;
+    case PD_MLP_Z3: f = m->Z3; break;
+    case PD_MLP_A3: b = m->A3; break;
+    case PD_MLP_OUT: f = m->out; n = (size_t)rows; break;
+    case PD_MLP_DOUT: f = m->dout; n = (size_t)rows; break;
+    case PD_MLP_DZ3: b = m->dZ3; break;
+    case PD_MLP_DA2: f = m->dA2; break;
+    case PD_MLP_DZ2: b = m->dZ2; break;
+    case PD_MLP_DA1: f = m->dA1; break;
+    case PD_MLP_DZ1: b = m->dZ1; break;
+    default: return fail(PD_EINVAL, "unknown buffer %d", which);
+    }
+    PD_CUDA(cudaStreamSynchronize(m->st));
+    if (f) {
+        PD_CUDA(cudaMemcpy(out, f, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<bf16> tmp(n);
+        PD_CUDA(cudaMemcpy(tmp.data(), b, sizeof(bf16) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) out[i] = __bfloat162float(tmp[i]);
+    }
     return PD_OK;
 }
 

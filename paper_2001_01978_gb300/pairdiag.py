@@ -17,6 +17,8 @@ from . import build as _build
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ENOCONV, PD_ETIMEOUT, PD_ECUDA, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 PD_PREC_FP64, PD_PREC_MIXED = 0, 1
 PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER, PD_START_MLP = 0, 1, 2, 3, 4
+(PD_MLP_Z1, PD_MLP_A1, PD_MLP_Z2, PD_MLP_A2, PD_MLP_Z3, PD_MLP_A3, PD_MLP_OUT, PD_MLP_DOUT, PD_MLP_DZ3, PD_MLP_DA2,
+ PD_MLP_DZ2, PD_MLP_DA1, PD_MLP_DZ1) = range(13)
 
 
 class pairdiag_options(ctypes.Structure):
@@ -76,6 +78,7 @@ _SIGNATURES = {
     "pairdiag_occupations_dev": (ctypes.c_int, [_H, _P, _P]),
     "pairdiag_lowest_states_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, _P, _P,
                                                   ctypes.POINTER(pairdiag_info)]),
+    "pairdiag_mlp_buffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "pairdiag_truncate": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "pairdiag_kept_map_dev": (ctypes.c_int, [_H, _P]),
     "pairdiag_full_dim": (ctypes.c_int64, [_H]),
@@ -516,6 +519,15 @@ def pairdiag_mlp_loss_grad(m, X, target):
     return loss.value, grad
 
 
+def pairdiag_mlp_buffer(m, which: int, rows: int) -> np.ndarray:
+    """An intermediate of the last pass (PD_MLP_*) as float32: [rows, 128], or
+    [rows] for PD_MLP_OUT and PD_MLP_DOUT."""
+    n = rows if which in (PD_MLP_OUT, PD_MLP_DOUT) else rows * 128
+    out = np.empty(n, dtype=np.float32)
+    _check(lib().pairdiag_mlp_buffer(m, which, rows, _np_ptr(out)))
+    return out if which in (PD_MLP_OUT, PD_MLP_DOUT) else out.reshape(rows, 128)
+
+
 def pairdiag_mlp_train(m, X, target, steps: int, lr: float = 1e-3) -> np.ndarray:
     X = np.ascontiguousarray(X, dtype=np.float32)
     t = np.ascontiguousarray(target, dtype=np.float32)
@@ -556,7 +568,7 @@ def pairdiag_autotune(omega: int, n_pairs: int, e, G, precision: int = PD_PREC_M
     e = np.ascontiguousarray(e, dtype=np.float64)
     G = np.ascontiguousarray(G, dtype=np.float64)
     best = pairdiag_tune_entry()
-    cap = 16
+    cap = 64                                  # 6 block splits x 4 variants fit
     arr = (pairdiag_tune_entry * cap)()
     n = ctypes.c_int(cap)
     _check(lib().pairdiag_autotune(omega, n_pairs, _np_ptr(e), _np_ptr(G), precision, reps, ctypes.byref(best),

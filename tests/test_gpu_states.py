@@ -87,3 +87,25 @@ def test_single_state_is_the_ground_state_and_bad_k_is_rejected():
             with pytest.raises(pd.PairDiagError) as err:
                 pd.pairdiag_lowest_states_dev(s.h, k, 1e-12)
             assert err.value.code == pd.PD_EINVAL
+
+
+def test_degenerate_level_full_size_omega24():
+    """Omega=24, N=12 (dim 2.7e6) on one degenerate level, mixed form: the lowest
+    three states are the quasispin level t = 0 and two copies of t = 1,
+    E_t = 2 eps N + g [N (Omega - N + 1) - t (Omega + 1 - t)] (a closed form, so
+    this pins the locking path at a size where the window leaves L2); the
+    returned vectors are orthonormal."""
+    omega, n, eps, g = 24, 12, 0.3, -0.25
+    e = np.full(omega, eps)
+    G = np.full((omega, omega), g)
+    dim = math.comb(omega, n)
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED, window=20) as s:
+        vecs = torch.empty(3 * dim, dtype=torch.float64, device="cuda")
+        r = pd.pairdiag_lowest_states_dev(s.h, 3, 1e-9, vecs)
+        V = vecs.view(3, dim)
+        gram = (V @ V.T).cpu().numpy()
+    assert r["status"] == pd.PD_OK
+    E = lambda t: 2 * eps * n + g * (n * (omega - n + 1) - t * (omega + 1 - t))
+    expect = [E(0), E(1), E(1)]
+    assert np.allclose(r["energies"], expect, rtol=1e-8, atol=0), (r["energies"], expect)
+    assert np.allclose(gram, np.eye(3), atol=1e-7)
