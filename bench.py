@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solves")
+    ap.add_argument("--states", action="store_true",
+                    help="the three lowest states of the default workload (locking), mixed and FP64")
     ap.add_argument("--truncate", action="store_true",
                     help="truncated model space (Sec. 3.5): E0 and time at nested Dimension_Limit values")
     ap.add_argument("--hx-only", action="store_true",
@@ -772,33 +774,41 @@ def run_odd(args):
     """Odd-mass twin of the default workload: 25 orbits (separable G plus noise, seed
     1), 12 pairs and one unpaired particle, every blocked subspace solved (the
     paper's Block = 0, Eq. 3): 25 subspaces of C(24,12) = 2.7e6 states each.
-    Time to the lowest E_b, plain FP64 vs the mixed form, same tolerance."""
+    Time to the lowest E_b: plain FP64, the mixed form, and the mixed form from
+    the learned warm start (the network trained once, outside the timing), same
+    tolerance."""
     import torch
     import paper_2001_01978_gb300 as pd
     torch.cuda.set_device(0)
+    ws = None if args.no_mlp else train_warm_start(args.train_problems, args.train_steps)[0]
     omega, n = 25, 12
     e, G = pd_inputs.separable_noise(omega, seed=1)
     dim = math.comb(omega - 1, n)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = {}
     clocks = ClockSampler(0)
-    for name, prec in (("mixed", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
-        opt = pd.pairdiag_default_options(precision=prec, window=args.window, seed=1)
+    forms = [("mixed", pd.PD_PREC_MIXED, pd.PD_START_RANDOM), ("fp64", pd.PD_PREC_FP64, pd.PD_START_RANDOM)]
+    if ws is not None:
+        forms.insert(0, ("mixed_mlp", pd.PD_PREC_MIXED, pd.PD_START_MLP))
+    for name, prec, start in forms:
+        opt = pd.pairdiag_default_options(precision=prec, window=args.window, seed=1, start=start)
+        mlp = ws.m if start == pd.PD_START_MLP else None
         for _ in range(args.warmup):
-            pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, want_vector=False)
+            pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, mlp=mlp, want_vector=False)
         times, r = [], None
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, want_vector=False)
+            r = pd.pairdiag_odd_ground_state(omega, n, e, G, args.tol, opt=opt, mlp=mlp, want_vector=False)
             times.append((time.perf_counter() - t0) * 1e3)
         ms = statistics.median(times)
         out[name] = {"time_to_e0_ms": ms, "ms_per_subspace": ms / omega, "e0": r["e0"], "block": r["block"],
                      "winner_iterations": r["iterations"], "winner_rel_residual": r["rel_residual"],
                      "status": r["status"], "energies": [float(x) for x in r["energies"]]}
     clk = clocks.stop()
-    out["mixed"]["e0_rel_diff_vs_fp64"] = abs(out["mixed"]["e0"] - out["fp64"]["e0"]) / abs(out["fp64"]["e0"])
+    for k in out:
+        out[k]["e0_rel_diff_vs_fp64"] = abs(out[k]["e0"] - out["fp64"]["e0"]) / abs(out["fp64"]["e0"])
     # the oracle's E_b of one subspace (committed by tests/golden/make_golden.py)
     oracle_b = {}
     for f in sorted((ROOT / "tests" / "golden").glob(f"omega{omega}_n{n}_sepnoise_s1_odd_b*_e0.txt")):
@@ -811,21 +821,66 @@ def run_odd(args):
     print(json.dumps({"odd_mass": True, "workload": "25 orbits, 12 pairs + 1 particle, separable G + noise, seed 1",
                       "subspaces": omega, "dim_per_subspace": dim, "tol": args.tol, "window": args.window,
                       "steps": args.steps, "warmup": args.warmup, "timing": "host wall clock around the "
-                      "synchronous call (it solves the subspaces one after another)",
+                      "synchronous call (three host threads solve the subspaces, each on its own stream)",
                       "l2": "flushed between calls", "forms": out, "clocks": clk,
-                      "speedup_mixed_vs_fp64": out["fp64"]["time_to_e0_ms"] / out["mixed"]["time_to_e0_ms"]}))
+                      "speedup_mixed_vs_fp64": out["fp64"]["time_to_e0_ms"] / out["mixed"]["time_to_e0_ms"],
+                      "speedup_mixed_mlp_vs_fp64": (out["fp64"]["time_to_e0_ms"] / out["mixed_mlp"]["time_to_e0_ms"]
+                                                    if "mixed_mlp" in out else None)}))
+    if ws is not None:
+        ws.close()
+    return 0
+
+
+def run_states(args):
+    """The lowest few states (Sec. 3.4, locking) of the default Omega=24 workload:
+    time to the three lowest eigenpairs in the mixed form and in FP64 (tol 1e-8),
+    the energies, and the orthonormality of the returned vectors."""
+    import torch
+    import paper_2001_01978_gb300 as pd
+    torch.cuda.set_device(0)
+    omega, n, e, G = pd_inputs.workload(args.workload)
+    dim = math.comb(omega, n)
+    k = 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    clocks = ClockSampler(0)
+    for name, prec in (("mixed", pd.PD_PREC_MIXED), ("fp64", pd.PD_PREC_FP64)):
+        with pd.Solver(omega, n, e, G, precision=prec, window=args.window, seed=1) as s:
+            pd.pairdiag_set_stream(s.h, stream)
+            vecs = torch.empty(k * dim, dtype=torch.float64, device="cuda")
+            for _ in range(args.warmup):
+                pd.pairdiag_lowest_states_dev(s.h, k, 1e-8, vecs)
+            times, r = [], None
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                r = pd.pairdiag_lowest_states_dev(s.h, k, 1e-8, vecs)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+            V = vecs.view(k, dim)
+            gram = (V @ V.T).cpu().numpy()
+        out[name] = {"ms": statistics.median(times), "energies": [float(x) for x in r["energies"]],
+                     "iterations": [i["iterations"] for i in r["info"]], "status": r["status"],
+                     "max_offdiag_overlap": float(np.max(np.abs(gram - np.eye(k))))}
+    clk = clocks.stop()
+    print(json.dumps({"lowest_states": True, "workload": args.workload, "dim": dim, "k": k, "tol": 1e-8,
+                      "window": args.window, "steps": args.steps, "l2": "flushed between calls", "forms": out,
+                      "clocks": clk}))
     return 0
 
 
 def main():
     args = parse_args()
     mode = ("batch" if args.batch else "warm" if args.warm else "big" if args.big else "odd" if args.odd else
-            "truncate" if args.truncate else
+            "truncate" if args.truncate else "states" if args.states else
             "hx" if args.hx_only and args.impl != "reference" else "line")
     if args.steps is None:
-        args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10, "odd": 3}.get(mode, 30)
+        args.steps = {"batch": 2, "warm": 3, "big": 1, "hx": 10, "odd": 3, "states": 3, "truncate": 1}.get(mode, 30)
     if args.warmup is None:
-        args.warmup = 1 if mode in ("big", "odd") else 3
+        args.warmup = 1 if mode in ("big", "odd", "states", "truncate") else 3
     if args.batch:
         return run_batch(args)
     if args.warm:
@@ -836,6 +891,8 @@ def main():
         return run_odd(args)
     if args.truncate:
         return run_truncate(args)
+    if args.states:
+        return run_states(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.hx_only:

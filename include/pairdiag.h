@@ -82,8 +82,9 @@ typedef struct {
                                once, 3 = no staging, every target gathered from global memory
                                with O(1) hop tables, 4 = variant 3 with the gathers issued in
                                deep groups (far from half filling, where a thread has one row
-                               and x is in DRAM); 2-4 fall back to 1 when their shared memory
-                               does not fit.  A truncated handle (pairdiag_truncate) runs
+                               and x is in DRAM), 5 = variant 3 compiled for 5 resident
+                               CTAs per SM (fewer registers, more warps); 2-5 fall back to 1
+                               when their shared memory does not fit.  A truncated handle (pairdiag_truncate) runs
                                variant 1 */
 } pairdiag_options;
 
@@ -419,7 +420,7 @@ int pairdiag_odd_ground_state(int omega, int n_pairs, const double *e, const dou
 /*
  * H*x schedule autotuner (an addition of this library; the paper has a single
  * CPU code path).  For one problem and precision it times the H*x kernel for
- * every block split L = low_bits in [min(omega,8), min(omega,13)] and the four
+ * every block split L = low_bits in [min(omega,8), min(omega,13)] and the five
  * kernel variants (median of `reps` launches on a random vector, CUDA events)
  * and records the fastest (low_bits, hx_variant) for (omega, n_pairs,
  * precision) in a process-wide table.  pairdiag_create and the batched solver

@@ -710,7 +710,7 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
     if (o.mode != 0 && o.mode != 1) return fail(PD_EINVAL, "bad mode");
     if (o.low_bits < 0 || o.low_bits > kMaxLow) return fail(PD_EINVAL, "low_bits outside 0..%d", kMaxLow);
     if (o.max_restarts < 0) return fail(PD_EINVAL, "max_restarts < 0");
-    if (o.hx_variant < 0 || o.hx_variant > 4) return fail(PD_EINVAL, "hx_variant outside 0..4");
+    if (o.hx_variant < 0 || o.hx_variant > 5) return fail(PD_EINVAL, "hx_variant outside 0..5");
     if (o.start < PD_START_RANDOM || o.start > PD_START_MLP) return fail(PD_EINVAL, "bad start kind");
 
     if (o.low_bits == 0 && o.hx_variant == 0) {   // an autotuned schedule, if one was recorded
@@ -1235,7 +1235,7 @@ int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int L = lmin; L <= lmax && rc == PD_OK; ++L) {
-        for (int variant = 1; variant <= 4 && rc == PD_OK; ++variant) {
+        for (int variant = 1; variant <= 5 && rc == PD_OK; ++variant) {
             pairdiag_options o;
             pairdiag_default_options(&o);
             o.low_bits = L;
@@ -1290,7 +1290,7 @@ int pairdiag_autotune(int omega, int n_pairs, const double *e, const double *G, 
 
 int pairdiag_tune_set(int omega, int n_pairs, int precision, int low_bits, int hx_variant_)
 {
-    if (low_bits < 0 || low_bits > kMaxLow || hx_variant_ < 0 || hx_variant_ > 4) return fail(PD_EINVAL, "bad schedule");
+    if (low_bits < 0 || low_bits > kMaxLow || hx_variant_ < 0 || hx_variant_ > 5) return fail(PD_EINVAL, "bad schedule");
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     if (low_bits == 0) g_tune.erase(TuneKey{omega, n_pairs, precision});
     else g_tune[TuneKey{omega, n_pairs, precision}] = {low_bits, hx_variant_};

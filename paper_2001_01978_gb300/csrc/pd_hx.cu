@@ -1124,8 +1124,10 @@ __device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega,
     else hx3_rows<T, A, R, DEEP>(s, omega, L, h, base, lw, y, swdot, k, ph, nemp, nhh, nk);
 }
 
-template <typename T, typename A, int R, bool DEEP>
-__global__ void __launch_bounds__(kThreads, 4)
+// OCC: resident CTAs per SM the register budget is cut for (4: 64 registers;
+// 5: 48 registers, variant 5, more warps to hide the gathers' latency)
+template <typename T, typename A, int R, bool DEEP, int OCC = 4>
+__global__ void __launch_bounds__(kThreads, OCC)
 hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, const T *__restrict__ x,
            T *__restrict__ y, Tickets *tk, const int *__restrict__ skip, double *blk_part, double *dot_out)
 {
@@ -1174,12 +1176,12 @@ bool use_v2(const Blocks &B)
     return layout2<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh, B.max_stage).total <= kSmemLimit;
 }
 
-// Variant 3 (lean loops) or 4 (deep gather groups) on request, when the shared
-// memory fits (full space only)
+// Variant 3 (lean loops), 4 (deep gather groups) or 5 (lean loops, 5 CTAs per
+// SM) on request, when the shared memory fits (full space only)
 template <typename T, typename A>
 bool use_v3(const Blocks &B)
 {
-    if ((B.variant != 3 && B.variant != 4) || B.kept_map) return false;
+    if ((B.variant < 3 || B.variant > 5) || B.kept_map) return false;
     return layout3<T, A>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total <= kSmemLimit;
 }
 
@@ -1188,7 +1190,9 @@ const void *kernel_fn(const Blocks &B)
 {
     if (B.kept_map) return (const void *)hx_kernel<T, A, R, true>;
     if (use_v3<T, A>(B))
-        return B.variant == 4 ? (const void *)hx3_kernel<T, A, R, true> : (const void *)hx3_kernel<T, A, R, false>;
+        return B.variant == 4   ? (const void *)hx3_kernel<T, A, R, true>
+               : B.variant == 5 ? (const void *)hx3_kernel<T, A, R, false, 5>
+                                : (const void *)hx3_kernel<T, A, R, false>;
     return use_v2<T, A>(B) ? (const void *)hx2_kernel<T, A, R> : (const void *)hx_kernel<T, A, R, false>;
 }
 
@@ -1217,6 +1221,9 @@ cudaError_t launch_t(const Blocks &B, const A *G, const A *d, const void *x, voi
     else if (use_v3<T, A>(B) && B.variant == 4)
         hx3_kernel<T, A, R, true><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                                 static_cast<T *>(y), tk, skip, bp, out);
+    else if (use_v3<T, A>(B) && B.variant == 5)
+        hx3_kernel<T, A, R, false, 5><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
+                                                                    static_cast<T *>(y), tk, skip, bp, out);
     else if (use_v3<T, A>(B))
         hx3_kernel<T, A, R, false><<<grid, kThreads, smem, st>>>(B, G, d, static_cast<const T *>(x),
                                                                  static_cast<T *>(y), tk, skip, bp, out);

@@ -568,7 +568,7 @@ def pairdiag_autotune(omega: int, n_pairs: int, e, G, precision: int = PD_PREC_M
     e = np.ascontiguousarray(e, dtype=np.float64)
     G = np.ascontiguousarray(G, dtype=np.float64)
     best = pairdiag_tune_entry()
-    cap = 64                                  # 6 block splits x 4 variants fit
+    cap = 64                                  # 6 block splits x 5 variants fit
     arr = (pairdiag_tune_entry * cap)()
     n = ctypes.c_int(cap)
     _check(lib().pairdiag_autotune(omega, n_pairs, _np_ptr(e), _np_ptr(G), precision, reps, ctypes.byref(best),

@@ -166,13 +166,14 @@ def test_hx_fp32_vs_oracle(omega, n, low):
         assert np.all(np.abs(got - ref) <= bound)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("omega,n,low", [(16, 5, 0), (20, 10, 0), (19, 9, 3), (15, 7, 8), (22, 4, 0), (24, 12, 13),
                                          (26, 3, 12), (21, 2, 9), (18, 16, 10), (12, 6, 12), (23, 1, 8), (20, 19, 11)])
 def test_hx_variants_vs_oracle(omega, n, low, variant):
-    """The four H*x kernel variants (neighbour blocks staged one at a time / all
+    """The five H*x kernel variants (neighbour blocks staged one at a time / all
     at once / gathered from global memory with O(1) hop tables, in lean loops or
-    in deep gather groups), including low and high filling, a single block
+    in deep gather groups, and the lean loops built for five CTAs per SM),
+    including low and high filling, a single block
     (L = Omega) and N = 1, Omega - 1."""
     e, G = pd_inputs.separable_noise(omega, seed=omega + 7 * n)
     b = oracle.basis(omega, n)

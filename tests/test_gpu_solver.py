@@ -31,7 +31,7 @@ def solve(omega, n, e, G, tol=1e-12, **opt):
 
 
 # --------------------------------------------------------------- FP64 -------
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("omega,n,low", [(16, 5, 10), (18, 3, 9), (14, 7, 0)])
 def test_solver_hx_variants_fp64(omega, n, low, variant):
     """Each H*x kernel variant inside the Lanczos step (its fused alpha dot
