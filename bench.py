@@ -733,7 +733,8 @@ def run_batch(args):
                 picks_ref[int(row[0])] = float(row[4])
     out = {}
     for name, prec, start in forms:
-        opt = pd.pairdiag_default_options(precision=prec, window=args.window, start=start)
+        opt = pd.pairdiag_default_options(precision=prec, window=args.window, start=start,
+                                          hx_variant=args.hx_variant)
         mlp = ws.m if start == pd.PD_START_MLP else None
         for _ in range(max(1, args.warmup // 3)):
             pd.pairdiag_batch_ground_state(probs, args.tol, opt, stream, mlp)

@@ -77,7 +77,9 @@ typedef struct {
     int      low_bits;      /* orbits handled inside one basis block (0 = automatic) */
     double   mixed_floor;   /* relative residual at which FP32 cycles hand over to FP64
                                refinement (PD_PREC_MIXED only); default 5e-6 */
-    int      hx_variant;    /* H*x kernel: 0 = automatic (default, currently 1), 1 = neighbour
+    int      hx_variant;    /* H*x kernel: 0 = automatic (default: the autotuned schedule if
+                               one was recorded, else 3, or 4 with 13 low orbits when fewer
+                               than 3 in 10 orbits are occupied or fewer than 3 in 10 empty), 1 = neighbour
                                blocks staged one at a time, 2 = all neighbour blocks staged at
                                once, 3 = no staging, every target gathered from global memory
                                with O(1) hop tables, 4 = variant 3 with the gathers issued in

@@ -717,6 +717,15 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
         int lb = 0, hv = 0;
         if (tuned_schedule(omega, n_pairs, o.precision, &lb, &hv)) { o.low_bits = lb; o.hx_variant = hv; }
     }
+    if (o.hx_variant == 0) {
+        // untuned: direct gathers; far from half filling (fewer than 3 in 10 orbits
+        // occupied, or empty) deep gather groups and 13 low orbits, the fastest
+        // schedules measured at Omega = 24..38
+        const int minority = std::min(n_pairs, omega - n_pairs);
+        const bool low_filling = 10 * minority < 3 * omega;
+        o.hx_variant = low_filling ? 4 : 3;
+        if (o.low_bits == 0 && low_filling) o.low_bits = 13;
+    }
     pairdiag *h = new pairdiag();
     h->omega = omega; h->n = n_pairs; h->opt = o;
     h->e.assign(e, e + omega);

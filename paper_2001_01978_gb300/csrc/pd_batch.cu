@@ -144,7 +144,7 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
     std::vector<int> chunk_prob, chunk_len, prob_chunk0, prob_nchunk;
     std::vector<int64_t> chunk_start, prob_off;
     int64_t total = 0;
-    int max_omega = 1, max_L = 1, max_H = 0, max_block = 1, max_hh = 0;
+    int max_omega = 1, max_L = 1, max_H = 0, max_block = 1, max_hh = 0, max_n = 0;
     for (int p = 0; p < count; ++p) {
         const int q = c.prob[p];
         const int om = omega[q], n = n_pairs[q];
@@ -177,6 +177,7 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
             }
         }
         const int64_t dim = (int64_t)host_binom(om, n);
+        max_n = std::max(max_n, n);
         BatchDesc &D = desc[p];
         D.omega = om; D.n = n; D.L = L;
         D.g_off = (int)G64.size(); D.d_off = (int)d64.size();
@@ -259,6 +260,9 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
     BB.blk_prob = d_bp; BB.blk_h = d_bh; BB.blk_base = d_bb; BB.desc = d_desc;
     BB.lowword_all = d_lw; BB.rankL_all = d_rk; BB.binom = d_binom;
     BB.max_omega = max_omega; BB.max_L = max_L; BB.max_H = max_H; BB.max_block = max_block; BB.max_hh = max_hh;
+    BB.max_n = max_n;
+    // the batched H*x: direct gathers (variant 3) unless the caller asks for the staged form
+    BB.variant = (opt.hx_variant == 1 || opt.hx_variant == 2) ? 1 : 3;
     BatchVec &V = c.V;
     V.count = count; V.nchunks = (int)chunk_prob.size(); V.total = total;
     V.chunk_prob = d_cp; V.chunk_start = d_cs; V.chunk_len = d_cl;

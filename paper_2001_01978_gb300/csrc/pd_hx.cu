@@ -1164,6 +1164,54 @@ hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, c
     hx_finish(tk, B.nblocks, blk_part, dot_out, sred);
 }
 
+// Batched form of variant 3: the blocks of many problems in one launch (the
+// global block list is sorted by problem).  A CTA reloads the problem's G, d,
+// rank table and binomials only when the next block it takes belongs to
+// another problem; problems flagged in skip[] are passed over.  The last CTA
+// returns both counters to zero.
+template <typename T, typename A, int R>
+__global__ void __launch_bounds__(kThreads, 4)
+hx3_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__restrict__ dall,
+                 const T *__restrict__ x, T *__restrict__ y, unsigned long long *counter,
+                 const int *__restrict__ skip, int skip_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_next;
+    const Smem3<T, A> s(smem, layout3<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh));
+    const int tid = threadIdx.x;
+    int cur = -1;
+    BatchDesc dsc{};
+    for (;;) {
+        __syncthreads();                          // smem of the previous block is free
+        if (tid == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long b = s_next;
+        if (b >= BB.nblocks) break;
+        const int pb = (int)__ldg(BB.blk_prob + b);
+        if (skip && skip[(int64_t)pb * skip_stride]) continue;   // CTA-uniform
+        if (pb != cur) {
+            dsc = BB.desc[pb];
+            const int om = dsc.omega, L = dsc.L, H = om - L, NB = dsc.n + 2;
+            const A *G = Gall + dsc.g_off;
+            const A *d = dall + dsc.d_off;
+            for (int i = tid; i < om * om; i += kThreads) s.G[i] = G[i];
+            for (int i = tid; i < om; i += kThreads) s.d[i] = d[i];
+            const uint16_t *rk = BB.rankL_all + dsc.tab_off;
+            for (int i = tid; i < (1 << L); i += kThreads) s.rank[i] = rk[i];
+            for (int i = tid; i < (H > 0 ? H : 1) * NB; i += kThreads) {
+                const int p = i / NB, m = i - p * NB;
+                s.bin[i] = __ldg(BB.binom + (L + p) * kBinomStride + m);
+            }
+            cur = pb;
+            __syncthreads();
+        }
+        hx3_block<T, A, R, false>(s, dsc.omega, dsc.L, dsc.omega - dsc.L, dsc.n, __ldg(BB.blk_h + b),
+                                  __ldg(BB.blk_base + b), BB.lowword_all + dsc.tab_off, x + dsc.vec_off,
+                                  y + dsc.vec_off, nullptr);
+    }
+    if (arrive_last(counter + 1) && tid == 0) counter[0] = 0ull;
+}
+
 constexpr size_t kSmemLimit = 200 * 1024;
 
 // Variant 2 only on request (the autotuner's choice, or the caller's) and when
@@ -1491,14 +1539,33 @@ cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const 
 }
 
 namespace {
+// the batched variant-3 kernel when asked for and its shared memory fits
+template <typename T, typename A>
+bool batch_v3(const BatchBlocks &BB)
+{
+    return BB.variant == 3 &&
+           layout3<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh).total <= kSmemLimit;
+}
+
 template <typename T, typename A, int R>
-const void *batch_fn() { return (const void *)hx_batch_kernel<T, A, R>; }
+const void *batch_fn(bool v3)
+{
+    return v3 ? (const void *)hx3_batch_kernel<T, A, R> : (const void *)hx_batch_kernel<T, A, R>;
+}
 
 template <typename T, typename A>
-const void *batch_fn_rows(int rows)
+const void *batch_fn_rows(int rows, bool v3)
 {
-    return rows <= 1 ? batch_fn<T, A, 1>() : rows <= 2 ? batch_fn<T, A, 2>() : rows <= 4 ? batch_fn<T, A, 4>()
-                                                                                          : batch_fn<T, A, 8>();
+    return rows <= 1 ? batch_fn<T, A, 1>(v3) : rows <= 2 ? batch_fn<T, A, 2>(v3) : rows <= 4 ? batch_fn<T, A, 4>(v3)
+                                                                                            : batch_fn<T, A, 8>(v3);
+}
+
+template <typename T, typename A>
+size_t batch_smem(const BatchBlocks &BB)
+{
+    return batch_v3<T, A>(BB)
+               ? layout3<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh).total
+               : layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh).total;
 }
 
 template <typename T, typename A>
@@ -1506,13 +1573,22 @@ cudaError_t batch_launch_t(const BatchBlocks &BB, const A *G, const A *d, const 
                            unsigned long long *counter, int grid, cudaStream_t st, const int *skip,
                            int skip_stride)
 {
-    const size_t smem = layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh).total;
+    const bool v3 = batch_v3<T, A>(BB);
+    const size_t smem = batch_smem<T, A>(BB);
     const int rows = (BB.max_block + kThreads - 1) / kThreads;
-    cudaError_t err = cudaFuncSetAttribute(batch_fn_rows<T, A>(rows),
+    cudaError_t err = cudaFuncSetAttribute(batch_fn_rows<T, A>(rows, v3),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const T *xt = static_cast<const T *>(x);
     T *yt = static_cast<T *>(y);
+    if (v3) {
+        if (rows <= 1) hx3_batch_kernel<T, A, 1><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+        else if (rows <= 2) hx3_batch_kernel<T, A, 2><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+        else if (rows <= 4) hx3_batch_kernel<T, A, 4><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+        else hx3_batch_kernel<T, A, 8><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     if (rows <= 1) hx_batch_kernel<T, A, 1><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
     else if (rows <= 2) hx_batch_kernel<T, A, 2><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
     else if (rows <= 4) hx_batch_kernel<T, A, 4><<<grid, kThreads, smem, st>>>(BB, G, d, xt, yt, counter, skip, skip_stride);
@@ -1524,8 +1600,8 @@ cudaError_t batch_launch_t(const BatchBlocks &BB, const A *G, const A *d, const 
 template <typename T, typename A>
 int batch_grid_t(const BatchBlocks &BB)
 {
-    const size_t smem = layout<T, A>(BB.max_omega, BB.max_L, BB.max_H, BB.max_block, BB.max_hh).total;
-    const void *fn = batch_fn_rows<T, A>((BB.max_block + kThreads - 1) / kThreads);
+    const size_t smem = batch_smem<T, A>(BB);
+    const void *fn = batch_fn_rows<T, A>((BB.max_block + kThreads - 1) / kThreads, batch_v3<T, A>(BB));
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

@@ -115,6 +115,8 @@ struct BatchBlocks {
     const uint16_t *rankL_all;
     const uint64_t *binom;
     int max_omega, max_L, max_H, max_block, max_hh;   // bounds for the shared-memory layout
+    int max_n;                       // largest number of pairs
+    int variant;                     // 1: neighbour blocks staged per hop class; 3: direct gathers
 };
 
 // Counters of a handle's kernels (device memory, zero when allocated).  Every
