@@ -477,6 +477,20 @@ int pairdiag_set_profiling(pairdiag_t *h, int on);
 int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms);
 
 /*
+ * Form of the vector work of one Lanczos step after its product (Algorithm 2
+ * with full reorthogonalisation, Sec. 3.4: the three-term recurrence, one
+ * Gram-Schmidt pass against every vector of the window, the norm, the scaling
+ * into the next basis vector).  on != 0 (default): one cooperative launch with
+ * two grid-wide barriers, each CTA keeping its slice of the work vector in
+ * shared memory where it fits; a barrier wait that gives up (after about a
+ * second) makes the solve return PD_ETIMEOUT.  on == 0: three launches (two
+ * streaming kernels whose sums are finished by their last CTA, and the
+ * scaling).  Devices without cooperative launch always take the second form.
+ * The results agree to rounding.  Applies from the next solve.
+ */
+int pairdiag_set_step_fusion(pairdiag_t *h, int on);
+
+/*
  * Fused multiply-add throughput of the current device in the arithmetic of
  * one H*x nonzero (PD_PREC_FP64: FP64 FMA; PD_PREC_MIXED: FP32 FMA): a kernel of
  * independent FMA chains on every SM, timed with CUDA events on `stream` after

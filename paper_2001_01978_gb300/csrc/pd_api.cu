@@ -170,6 +170,11 @@ struct pairdiag {
     float *d_L32 = nullptr;          // their FP32 copies (mixed form)
     double *d_lockc = nullptr;       // [kMaxWindow] projection coefficients
     pairdiag_mlp *mlp = nullptr;     // network predicting them (PD_START_MLP)
+    // the fused Lanczos step (one cooperative launch per step) per storage type;
+    // planned for the window buffer step_q[dtype]
+    bool step_fusion = true;
+    StepPlan step[2];
+    const void *step_q[2] = {nullptr, nullptr};
     // optional event timing of H*x launches
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> hx_events;
@@ -368,6 +373,17 @@ int lock_project(pairdiag *h, int dtype, void *v, const int *skip)
     return PD_OK;
 }
 
+// err: the barrier error flag, copied back with the cycle's scalars.
+// PD_ETIMEOUT (and the barrier state reset) when a grid-wide wait of a fused
+// step gave up.
+int check_barrier(pairdiag *h, int err)
+{
+    if (!err) return PD_OK;
+    PD_CUDA(cudaMemsetAsync(&h->d_tk->bar, 0, sizeof(GridBar), h->st));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return fail(PD_ETIMEOUT, "a grid-wide barrier of the fused Lanczos step timed out");
+}
+
 struct CycleStats {
     int iterations = 0;
     int restarts = 0;
@@ -377,18 +393,33 @@ struct CycleStats {
     bool converged = false;
 };
 
-// One Lanczos step i on storage type dtype (Algorithm 2 with full
-// reorthogonalisation, Sec. 3.4), three launches:
+// The fused step's plan for the current window buffer of dtype; false where
+// the three-kernel form runs instead
+bool fused_step(pairdiag *h, int dtype)
+{
+    if (!h->step_fusion) return false;
+    if (h->step_q[dtype] != h->d_Q[dtype]) {
+        h->step[dtype] = StepPlan{};
+        step_plan(dtype, h->dim, h->ldq, h->d_Q[dtype], h->d_p[dtype], &h->step[dtype]);
+        h->step_q[dtype] = h->d_Q[dtype];
+    }
+    return h->step[dtype].grid > 0;
+}
+
+// One Lanczos step i of a cycle of m on storage type dtype (Algorithm 2 with
+// full reorthogonalisation, Sec. 3.4):
 //   1. p = H q_i and alpha = q_i^T p (the dot fused into the H*x launch);
-//   2. the three-term recurrence p -= alpha q_i + beta_{i-1} q_{i-1} fused with
-//      the projections c = Q^T p of one Gram-Schmidt pass against every stored
+//   2. the three-term recurrence p -= alpha q_i + beta_{i-1} q_{i-1} with the
+//      projections c = Q^T p of one Gram-Schmidt pass against every stored
 //      vector;
-//   3. p -= Q c with ||p||^2, then alpha_i = alpha + c_i, beta_i = ||p||.
-// The recurrence followed by the full pass is Gram-Schmidt applied twice.  The
-// sums of launches 2 and 3 are finished by their last CTA (no separate
-// reduction launch).  Every kernel is skipped once S->broken is set
-// (breakdown earlier in the cycle).
-int lanczos_step(pairdiag *h, int dtype, int i)
+//   3. p -= Q c with ||p||^2, then alpha_i = alpha + c_i, beta_i = ||p||;
+//   4. q_{i+1} = p / beta_i (i + 1 < m).
+// The recurrence followed by the full pass is Gram-Schmidt applied twice.
+// Fused form: 2-4 are one cooperative launch with grid-wide barriers.  Else
+// 2 and 3 are two launches whose sums are finished by their last CTA, and 4
+// is the scaling at the start of the next step.  Every kernel is skipped once
+// S->broken is set (breakdown or a converged Ritz estimate earlier in the cycle).
+int lanczos_step(pairdiag *h, int dtype, int i, int m)
 {
     const int64_t dim = h->dim;
     LanczosScalars *S = h->d_S;
@@ -400,6 +431,11 @@ int lanczos_step(pairdiag *h, int dtype, int i)
     unsigned long long *tk = &h->d_tk->vec_done;
     PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip, S->c1));
     if (h->n_locked) PD_TRY(lock_project(h, dtype, p, skip));
+    if (fused_step(h, dtype)) {
+        PD_CUDA(step_launch(dtype, h->step[dtype], Q, ld, i, S, p, dim, h->d_part, &h->d_tk->bar,
+                            i + 1 < m ? qvec(h, dtype, i + 1) : nullptr, st));
+        return PD_OK;
+    }
     PD_CUDA(recur_project_launch(dtype, Q, ld, i, S, p, dim, h->d_part, S->c2, st, skip, tk));
     PD_CUDA(update_launch(dtype, Q, ld, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip, tk, S, i));
     return PD_OK;
@@ -435,11 +471,14 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
             PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->dots[0], 1, st));
         }
         PD_CUDA(cycle_reset_launch(S, st));
-        PD_TRY(lanczos_step(h, dtype, 0));
+        PD_TRY(lanczos_step(h, dtype, 0, m));
         double ab[2];
         PD_CUDA(cudaMemcpyAsync(&ab[0], &S->alpha[0], sizeof(double), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaMemcpyAsync(&ab[1], &S->beta[0], sizeof(double), cudaMemcpyDeviceToHost, st));
+        int berr = 0;
+        PD_CUDA(cudaMemcpyAsync(&berr, &h->d_tk->bar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaStreamSynchronize(st));
+        PD_TRY(check_barrier(h, berr));
         ++cs.iterations;
         if (!std::isfinite(ab[0]) || !std::isfinite(ab[1]))
             return fail(PD_ECUDA, "non-finite Lanczos coefficient in cycle %d", cycle);
@@ -460,9 +499,10 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         // failed (the estimate was optimistic, e.g. near the rounding floor of
         // the vectors): later cycles stop only at a 4x smaller estimate
         if (ended_early) est_tol *= 0.25;
+        const bool fused = fused_step(h, dtype);
         for (int i = 1; i < m; ++i) {
-            PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));
-            PD_TRY(lanczos_step(h, dtype, i));
+            if (!fused) PD_CUDA(scale_launch(dtype, p, qvec(h, dtype, i), dim, &S->beta[i - 1], 0, st, skip));
+            PD_TRY(lanczos_step(h, dtype, i, m));
             // restarted mode: end the cycle as soon as its lowest Ritz pair is
             // converged, instead of running the whole window
             if (h->opt.mode == 0 && (i + 1) % kRitzCheckEvery == 0 && i + 1 < m)
@@ -475,7 +515,9 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         int used = 0;
         PD_CUDA(cudaMemcpyAsync(th, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaMemcpyAsync(&used, &S->used, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaMemcpyAsync(&berr, &h->d_tk->bar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaStreamSynchronize(st));
+        PD_TRY(check_barrier(h, berr));
         cs.iterations += used - 1;
         ended_early = used < m;
         if (!std::isfinite(th[0])) return fail(PD_ECUDA, "non-finite Ritz value in cycle %d", cycle);
@@ -781,6 +823,13 @@ int pairdiag_set_profiling(pairdiag_t *h, int on)
 {
     if (!h) return fail(PD_EINVAL, "null handle");
     h->profiling = on != 0;
+    return PD_OK;
+}
+
+int pairdiag_set_step_fusion(pairdiag_t *h, int on)
+{
+    if (!h) return fail(PD_EINVAL, "null handle");
+    h->step_fusion = on != 0;
     return PD_OK;
 }
 

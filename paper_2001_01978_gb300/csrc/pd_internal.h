@@ -122,11 +122,18 @@ struct BatchBlocks {
 // Counters of a handle's kernels (device memory, zero when allocated).  Every
 // kernel that uses a field leaves it at zero when it finishes: the CTA that
 // arrives last resets it, so no memset is needed between launches.
+struct GridBar {                     // grid-wide barrier of a cooperative launch
+    unsigned int count;              // CTAs arrived at the current barrier
+    unsigned int gen;                // generation: opened by the last CTA to arrive
+    int err;                         // a wait gave up (the launch's results are void)
+    int pad;
+};
 struct Tickets {
     unsigned long long hx_next;      // next block of a persistent H*x launch
     unsigned long long hx_done;      // CTAs of that launch that have finished
     unsigned long long vec_done;     // CTAs of a streaming kernel whose partial sums are written
     unsigned long long pad;
+    GridBar bar;                     // the fused Lanczos step's barriers
 };
 
 #ifdef __CUDACC__
@@ -376,6 +383,24 @@ cudaError_t scale_launch(int dtype, const void *src, void *dst, int64_t n, const
 cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, const LanczosScalars *S,
                                  void *p, int64_t n, double *partials, double *out, cudaStream_t st,
                                  const int *skip = nullptr, unsigned long long *ticket = nullptr);
+// One Lanczos step after the product p = H q_i (alpha = S->c1[0]) in a single
+// cooperative launch: the recurrence, the projections c = Q^T p and
+// p -= Q c of one full Gram-Schmidt pass, ||p||, the step bookkeeping of
+// S (alpha_i, beta_i, tnorm, used, broken, c2) and, unless qnext is null or the
+// step broke down, qnext = p / beta_i.  Grid-wide barriers in between; a wait
+// that gives up sets gb->err.  step_plan returns 0 where no cooperative launch
+// is possible (the caller then takes the three-kernel form).
+struct StepPlan {
+    int grid = 0;                    // CTAs (all resident)
+    int64_t slice = 0;               // packs per CTA
+    bool packed = false;             // 16-byte packs
+    bool in_smem = false;            // each CTA keeps its slice of p in shared memory
+    size_t smem = 0;                 // dynamic shared memory per CTA
+};
+constexpr size_t kStepSmemMax = 192 * 1024;
+int step_plan(int dtype, int64_t n, int64_t ldq, const void *Q, const void *p, StepPlan *plan);
+cudaError_t step_launch(int dtype, const StepPlan &plan, const void *Q, int64_t ldq, int i, LanczosScalars *S,
+                        void *p, int64_t n, double *partials, GridBar *gb, void *qnext, cudaStream_t st);
 // start of a cycle: used = 0, broken = 0, tnorm = 0
 cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
 // after step i of a cycle: when the residual of the lowest Ritz pair of the

@@ -305,6 +305,339 @@ scale_kernel(const T *src, T *dst, int64_t n, const double *__restrict__ div, in
     }
 }
 
+// ---- one Lanczos step after the product, in one cooperative launch ---------
+// The recurrence, one full Gram-Schmidt pass against every stored vector, the
+// norm and the scaling into the next basis vector (Algorithm 2, Sec. 3.4) with
+// two grid-wide barriers in between instead of three launches.  CTA b owns
+// packs [b*slice, (b+1)*slice) of every vector; with SMEM its part of p stays in
+// shared memory from the recurrence to the scaling, so p is read once and never
+// written.  Every CTA adds the CTAs' partial sums in the same fixed order, so
+// all of them hold bit-identical coefficients.
+constexpr int kStepThreads = 512;
+constexpr int kStepWarps = kStepThreads / 32;
+constexpr unsigned kBarPolls = 1u << 24;      // x >= 64 ns: a barrier gives up after about a second
+
+// Dot-product accumulator of the step kernel, one pack at a time.  FP32: the
+// pack's W products are summed with FP32 FMAs and the pack sum is added to a
+// float-float total with Knuth's TwoSum (10 instructions per pack of 4 instead
+// of 32 for exact products).  The rounding of a pack sum is relative to that
+// pack's own products, so it stays far below the FP32 rounding of the stored
+// vectors.  FP64: FP64 FMAs.
+template <typename T> struct PackAcc;
+template <> struct PackAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    template <int W>
+    __device__ __forceinline__ void add(const Pack<float, W> &a, const Pack<float, W> &b)
+    {
+        float s = a.v[0] * b.v[0];
+#pragma unroll
+        for (int k = 1; k < W; ++k) s = fmaf(a.v[k], b.v[k], s);
+        const float t = hi + s;
+        const float z = t - hi;
+        lo += (hi - (t - z)) + (s - z);
+        hi = t;
+    }
+};
+template <> struct PackAcc<double> {
+    double v = 0.0;
+    template <int W>
+    __device__ __forceinline__ void add(const Pack<double, W> &a, const Pack<double, W> &b)
+    {
+#pragma unroll
+        for (int k = 0; k < W; ++k) v = fma(a.v[k], b.v[k], v);
+    }
+};
+
+// float-float (FP32) or FP64 partial sums of the step kernel
+template <typename T> struct StepRed;
+template <> struct StepRed<float> {
+    using P = float2;
+    static __device__ __forceinline__ P zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ P from(const PackAcc<float> &a) { return make_float2(a.hi, a.lo); }
+    static __device__ __forceinline__ void add(P &a, P b) { ff_add(a.x, a.y, b.x, b.y); }
+    static __device__ __forceinline__ P xor_shfl(P a, int o)
+    {
+        return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
+    static __device__ __forceinline__ double value(P a) { return (double)a.x + (double)a.y; }
+};
+template <> struct StepRed<double> {
+    using P = double;
+    static __device__ __forceinline__ P zero() { return 0.0; }
+    static __device__ __forceinline__ P from(const PackAcc<double> &a) { return a.v; }
+    static __device__ __forceinline__ void add(P &a, P b) { a += b; }
+    static __device__ __forceinline__ P xor_shfl(P a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double value(P a) { return a; }
+};
+
+template <typename R>
+__device__ __forceinline__ typename R::P warp_allsum(typename R::P s)
+{
+    for (int o = 16; o > 0; o >>= 1) R::add(s, R::xor_shfl(s, o));
+    return s;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  Thread 0
+// reads the generation before it arrives (acquire loads, release stores); the
+// last CTA to arrive resets the count and opens the next generation.  A wait
+// longer than kBarPolls polls sets gb->err and returns false (the caller
+// returns at once; the other CTAs then give up at this barrier or the next).
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *a)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int *a, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(GridBar *gb, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int g = ld_acquire_u32(&gb->gen);
+        __threadfence();                                     // release this CTA's writes
+        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1u) {
+            gb->count = 0u;
+            st_release_u32(&gb->gen, g + 1u);
+        } else {
+            unsigned int polls = 0;
+            while (ld_acquire_u32(&gb->gen) == g) {
+                if (++polls > kBarPolls) {
+                    atomicExch(&gb->err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (polls > 64) __nanosleep(32);
+            }
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// the packs c of the group's vectors Q_j0 .. Q_{j0+kGroup-1} that exist (j < m)
+template <typename T, int W>
+__device__ __forceinline__ void load_group(Pack<T, W> (&q)[kGroup], const T *__restrict__ Q, int64_t ldq, int j0,
+                                           int m, int64_t c, int64_t n)
+{
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u)
+        if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
+}
+
+// Ownership: the packs form chunks of kStepThreads; CTA b owns the K
+// consecutive chunks b*K .. b*K + K - 1, thread t pack t of each.  Local pack
+// slot (chunk l of the CTA, thread t) = l * kStepThreads + t.
+template <typename T, int W, bool SMEM>
+__global__ void __launch_bounds__(kStepThreads, 1)
+step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p, int64_t n,
+            typename StepRed<T>::P *part, GridBar *gb, T *qnext)
+{
+    using R = StepRed<T>;
+    using P = typename R::P;
+    extern __shared__ __align__(16) unsigned char step_smem[];
+    Pack<T, W> *sv = reinterpret_cast<Pack<T, W> *>(step_smem);   // this CTA's packs of p (SMEM)
+    __shared__ P wpart[kStepWarps][kMaxWindow];
+    __shared__ double sc[kMaxWindow];
+    __shared__ T scT[kMaxWindow];
+    __shared__ T s_ab[3];                         // alpha, beta_{i-1}, 1 / beta_i in the storage type
+    __shared__ double s_in[3];                    // alpha, beta_{i-1}, tnorm as the launch found them
+    __shared__ int s_ok, s_brk;
+    if (S->broken) return;                        // uniform: nothing in this launch writes it before the barriers
+    const int m = i + 1;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    // the FP64 scalars once per CTA (GB300 runs FP64 at a small fraction of
+    // FP32), read before the first barrier: block 0 rewrites tnorm after the last
+    if (tid == 0) {
+        s_in[0] = S->c1[0];
+        s_in[1] = i > 0 ? S->beta[i - 1] : 0.0;
+        s_in[2] = S->tnorm;
+        s_ab[0] = (T)s_in[0];
+        s_ab[1] = (T)s_in[1];
+    }
+    __syncthreads();
+    const T a = s_ab[0], b = s_ab[1];
+    const T *qi = Q + (int64_t)i * ldq;
+    const T *qm = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
+    const int64_t nc = (n + W - 1) / W;
+    const int64_t nchunk = (nc + kStepThreads - 1) / kStepThreads;
+    const int64_t G = gridDim.x;
+    const int64_t K = (nchunk + G - 1) / G;
+    const int64_t first = (int64_t)blockIdx.x * K;
+    const int64_t mine = first < nchunk ? (nchunk - first < K ? nchunk - first : K) : 0;   // chunks of this CTA
+    const int ng = (m + kGroup - 1) / kGroup;
+    auto pack_of = [&](int64_t l) { return (first + l) * kStepThreads + tid; };
+
+    // phase 1: p <- p - alpha q_i - beta_{i-1} q_{i-1}; c_j = Q_j^T p (j <= i).
+    // Two chunks per iteration, all their loads issued before the first use.
+    for (int g = 0; g < ng; ++g) {
+        const int j0 = g * kGroup;
+        PackAcc<T> acc[kGroup];
+        for (int64_t l = 0; l < mine; l += 2) {
+            const int64_t c0 = pack_of(l), c1 = pack_of(l + 1);
+            const bool ok0 = c0 < nc, ok1 = l + 1 < mine && c1 < nc;
+            Pack<T, W> v[2], q[2][kGroup];
+            if (g == 0) {
+                Pack<T, W> x[2], y[2];
+                if (ok0) {
+                    v[0] = load_pack<T, W, false>(p, c0, n);
+                    x[0] = load_pack<T, W, true>(qi, c0, n);
+                    y[0] = load_pack<T, W, true>(qm, c0, n);
+                    load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+                }
+                if (ok1) {
+                    v[1] = load_pack<T, W, false>(p, c1, n);
+                    x[1] = load_pack<T, W, true>(qi, c1, n);
+                    y[1] = load_pack<T, W, true>(qm, c1, n);
+                    load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(h == 0 ? ok0 : ok1)) continue;
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        v[h].v[k] = fma_t<T>(-b, y[h].v[k], fma_t<T>(-a, x[h].v[k], v[h].v[k]));
+                    if (SMEM) sv[(l + h) * kStepThreads + tid] = v[h];
+                    else store_pack<T, W>(p, h == 0 ? c0 : c1, n, v[h]);
+                }
+            } else {
+                if (ok0) {
+                    v[0] = SMEM ? sv[l * kStepThreads + tid] : load_pack<T, W, false>(p, c0, n);
+                    load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+                }
+                if (ok1) {
+                    v[1] = SMEM ? sv[(l + 1) * kStepThreads + tid] : load_pack<T, W, false>(p, c1, n);
+                    load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+                }
+            }
+            if (ok0) {
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) acc[u].add(q[0][u], v[0]);
+            }
+            if (ok1) {
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m) acc[u].add(q[1][u], v[1]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u)
+            if (j0 + u < m) {
+                const P s = warp_allsum<R>(R::from(acc[u]));
+                if (lane == 0) wpart[w][j0 + u] = s;
+            }
+    }
+    __syncthreads();
+    if (tid < m) {
+        P s = R::zero();
+        for (int x = 0; x < kStepWarps; ++x) R::add(s, wpart[x][tid]);
+        part[(int64_t)blockIdx.x * kMaxWindow + tid] = s;
+    }
+    if (!grid_sync(gb, &s_ok)) return;
+    // every CTA adds the CTAs' partial sums in the same order
+    for (int j = w; j < m; j += kStepWarps) {
+        P s = R::zero();
+        for (int x = lane; x < (int)G; x += 32) R::add(s, __ldcg(part + (int64_t)x * kMaxWindow + j));
+        s = warp_allsum<R>(s);
+        if (lane == 0) {
+            const double c = R::value(s);
+            sc[j] = c;
+            scT[j] = (T)c;
+        }
+    }
+    __syncthreads();
+
+    // phase 2: p <- p - sum_j c_j Q_j, the groups in reverse (the vectors phase 1
+    // read last are the likeliest still in L2), then ||p||^2
+    PackAcc<T> nrm;
+    for (int g = ng - 1; g >= 0; --g) {
+        const int j0 = g * kGroup;
+        T cg[kGroup];
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) cg[u] = (j0 + u < m) ? scT[j0 + u] : T(0);
+        for (int64_t l = 0; l < mine; l += 2) {
+            const int64_t c0 = pack_of(l), c1 = pack_of(l + 1);
+            const bool ok0 = c0 < nc, ok1 = l + 1 < mine && c1 < nc;
+            Pack<T, W> v[2], q[2][kGroup];
+            if (ok0) {
+                v[0] = SMEM ? sv[l * kStepThreads + tid] : load_pack<T, W, false>(p, c0, n);
+                load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+            }
+            if (ok1) {
+                v[1] = SMEM ? sv[(l + 1) * kStepThreads + tid] : load_pack<T, W, false>(p, c1, n);
+                load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!(h == 0 ? ok0 : ok1)) continue;
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if (j0 + u < m)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) v[h].v[k] = fma_t<T>(-cg[u], q[h][u].v[k], v[h].v[k]);
+                if (g == 0) nrm.add(v[h], v[h]);
+                if (SMEM) sv[(l + h) * kStepThreads + tid] = v[h];
+                else store_pack<T, W>(p, h == 0 ? c0 : c1, n, v[h]);
+            }
+        }
+    }
+    {
+        const P s = warp_allsum<R>(R::from(nrm));
+        if (lane == 0) wpart[w][0] = s;
+    }
+    __syncthreads();
+    P *npart = part + G * kMaxWindow;
+    if (tid == 0) {
+        P s = R::zero();
+        for (int x = 0; x < kStepWarps; ++x) R::add(s, wpart[x][0]);
+        npart[blockIdx.x] = s;
+    }
+    if (!grid_sync(gb, &s_ok)) return;
+    // the norm, and the step bookkeeping (the arithmetic of finalize_step) in one
+    // thread per CTA, every CTA alike
+    if (w == 0) {
+        P s = R::zero();
+        for (int x = lane; x < (int)G; x += 32) R::add(s, __ldcg(npart + x));
+        s = warp_allsum<R>(s);
+        if (lane == 0) {
+            const double norm2 = R::value(s);
+            const double ai = s_in[0] + sc[i];
+            const double bi = sqrt(norm2);
+            const double tn = fmax(s_in[2], fabs(ai) + bi + s_in[1]);
+            const int brk = !(bi > 1e-13 * tn);
+            s_brk = brk;
+            s_ab[2] = brk ? T(0) : (T)(1.0 / bi);
+            if (blockIdx.x == 0) {
+                S->norm2 = norm2;
+                S->alpha[i] = ai;
+                S->beta[i] = bi;
+                S->tnorm = tn;
+                S->used = i + 1;
+                if (brk) S->broken = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && tid < m) S->c2[tid] = sc[tid];
+    // phase 3: q_{i+1} = p / beta_i
+    if (s_brk || !qnext) return;
+    const T f = s_ab[2];
+    for (int64_t l = 0; l < mine; ++l) {
+        const int64_t cc = pack_of(l);
+        if (cc >= nc) continue;
+        Pack<T, W> v = SMEM ? sv[l * kStepThreads + tid] : load_pack<T, W, false>(p, cc, n);
+#pragma unroll
+        for (int k = 0; k < W; ++k) v.v[k] = v.v[k] * f;
+        store_pack<T, W>(qnext, cc, n, v);
+    }
+}
+
 __global__ void cycle_reset_kernel(LanczosScalars *S)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1130,9 +1463,100 @@ void ritz_t(T *Q, int64_t ld, const int *m_dev, const double *s, int64_t n, doub
     if (!ticket) reduce(part, g, 1, norm_out, st);
 }
 
+// the step kernel instance of a plan
+template <typename T>
+const void *step_fn(bool packed, bool in_smem)
+{
+    constexpr int W = kPackBytes / sizeof(T);
+    if (packed) return in_smem ? (const void *)step_kernel<T, W, true> : (const void *)step_kernel<T, W, false>;
+    return in_smem ? (const void *)step_kernel<T, 1, true> : (const void *)step_kernel<T, 1, false>;
+}
+
+template <typename T>
+size_t step_pack_bytes(bool packed)
+{
+    return packed ? (size_t)kPackBytes : sizeof(T);
+}
+
+template <typename T>
+int step_plan_t(int64_t n, int64_t ldq, const void *Q, const void *p, StepPlan *plan)
+{
+    plan->grid = 0;
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    const bool pk = packable<T>({Q, p}, ldq);
+    const int64_t units = pack_units<T>(n, pk);
+    const int64_t nchunk = (units + kStepThreads - 1) / kStepThreads;
+    // at least four chunks of kStepThreads packs per CTA, at most one CTA per SM
+    int64_t grid = std::min<int64_t>(std::max<int64_t>((nchunk + 3) / 4, 1), (int64_t)sm_count());
+    int64_t slice = (nchunk + grid - 1) / grid * kStepThreads;      // packs per CTA, whole chunks
+    const size_t smem = (size_t)slice * step_pack_bytes<T>(pk);
+    bool in_smem = smem <= kStepSmemMax;
+    const void *fn = step_fn<T>(pk, in_smem);
+    if (in_smem && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        in_smem = false;
+        fn = step_fn<T>(pk, false);
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, in_smem ? smem : 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (grid > (int64_t)per_sm * sm_count()) {     // fewer CTAs resident than planned: without the slice in shared memory
+        in_smem = false;
+        fn = step_fn<T>(pk, false);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, 0) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            return 0;
+        }
+        grid = std::min<int64_t>(grid, (int64_t)per_sm * sm_count());
+        slice = (nchunk + grid - 1) / grid * kStepThreads;
+    }
+    plan->grid = (int)grid;
+    plan->slice = slice;
+    plan->packed = pk;
+    plan->in_smem = in_smem;
+    plan->smem = in_smem ? (size_t)slice * step_pack_bytes<T>(pk) : 0;
+    return 1;
+}
+
+template <typename T>
+cudaError_t step_t(const StepPlan &plan, const T *Q, int64_t ldq, int i, LanczosScalars *S, T *p, int64_t n,
+                   double *part, GridBar *gb, T *qnext, cudaStream_t st)
+{
+    using P = typename StepRed<T>::P;
+    P *pp = reinterpret_cast<P *>(part);
+    void *args[] = {(void *)&Q, (void *)&ldq, (void *)&i, (void *)&S, (void *)&p, (void *)&n, (void *)&pp,
+                    (void *)&gb, (void *)&qnext};
+    const void *fn = step_fn<T>(plan.packed, plan.in_smem);
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(kStepThreads), args, plan.smem, st);
+    count_launches(1);
+    return e;
+}
+
 }  // namespace
 
 int vec_grid() { return grid_cap(); }
+
+int step_plan(int dtype, int64_t n, int64_t ldq, const void *Q, const void *p, StepPlan *plan)
+{
+    return dtype == 0 ? step_plan_t<double>(n, ldq, Q, p, plan) : step_plan_t<float>(n, ldq, Q, p, plan);
+}
+
+cudaError_t step_launch(int dtype, const StepPlan &plan, const void *Q, int64_t ldq, int i, LanczosScalars *S,
+                        void *p, int64_t n, double *partials, GridBar *gb, void *qnext, cudaStream_t st)
+{
+    if (plan.grid < 1) return cudaErrorInvalidValue;
+    if (dtype == 0)
+        return step_t<double>(plan, (const double *)Q, ldq, i, S, (double *)p, n, partials, gb, (double *)qnext, st);
+    return step_t<float>(plan, (const float *)Q, ldq, i, S, (float *)p, n, partials, gb, (float *)qnext, st);
+}
 
 cudaError_t multidot_launch(int dtype, const void *Q, int64_t ld, int m, const void *p, int64_t n,
                             double *partials, double *out, cudaStream_t st, const int *skip,

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "pairdiag_kernel_launches": (ctypes.c_int64, []),
     "pairdiag_release_cache": (ctypes.c_int, [_P]),
     "pairdiag_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
+    "pairdiag_set_step_fusion": (ctypes.c_int, [_H, ctypes.c_int]),
     "pairdiag_get_profile": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "pairdiag_batch_ground_state": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
                                                    ctypes.POINTER(pairdiag_options), _H, _P, _P, _P, _P]),
@@ -458,6 +459,11 @@ def pairdiag_release_cache() -> int:
 
 def pairdiag_set_profiling(h, on: bool) -> None:
     _check(lib().pairdiag_set_profiling(h, 1 if on else 0))
+
+
+def pairdiag_set_step_fusion(h, on: bool) -> None:
+    """One cooperative launch per Lanczos step (True, default) or three launches."""
+    _check(lib().pairdiag_set_step_fusion(h, 1 if on else 0))
 
 
 def pairdiag_get_profile(h, precision: int = PD_PREC_MIXED):
