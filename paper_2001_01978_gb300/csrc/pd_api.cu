@@ -355,6 +355,12 @@ int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nul
 template <typename T>
 T *vec(void *base, int64_t i, int64_t dim) { return static_cast<T *>(base) + i * dim; }
 
+// device scratch for the 2^L low-word factors of a product start vector
+double *factor_scratch(pairdiag *h)
+{
+    return h->part_count >= ((size_t)1 << h->B.L) ? h->d_part : nullptr;
+}
+
 void *qvec(pairdiag *h, int dtype, int i)
 {
     const size_t es = dtype == 0 ? 8 : 4;
@@ -567,7 +573,7 @@ int init_start(pairdiag *h, int dtype)
         if (h->mlp) PD_TRY(mlp_predict(h->mlp, h->omega, h->n, h->e.data(), h->G.data(), w.data()));
         else if ((int)h->start_w.size() == h->omega) w = h->start_w;
         else return fail(PD_EINVAL, "PD_START_MLP needs pairdiag_set_mlp or pairdiag_set_start_weights");
-        PD_TRY(product_start(h->B, w.data(), dtype, q0, h->st));
+        PD_TRY(product_start(h->B, w.data(), dtype, q0, h->st, factor_scratch(h)));
         break;
     }
     case PD_START_USER: {
@@ -952,7 +958,9 @@ int pairdiag_product_fit(pairdiag_t *h, const double *v_dev, double *w)
 int pairdiag_product_start_dev(pairdiag_t *h, const double *w, double *v_dev)
 {
     if (!h || !w || !v_dev) return fail(PD_EINVAL, "null argument");
-    return product_start(h->B, w, 0, v_dev, h->st);
+    PD_TRY(product_start(h->B, w, 0, v_dev, h->st, factor_scratch(h)));
+    PD_CUDA(cudaStreamSynchronize(h->st));
+    return PD_OK;
 }
 
 int pairdiag_set_start(pairdiag_t *h, const double *v)
@@ -1209,6 +1217,7 @@ int pairdiag_truncate(pairdiag_t *h, int64_t dimension_limit, int64_t bins, int6
             if (r0 != PD_OK) { pool_free(g1); return r0; }
             int r = ensure_fp64_pair(h);
             if (r == PD_OK) r = product_start(h->B, zeros.data(), 0, h->d_v64, h->st);   // kept entries = 1
+            if (r == PD_OK && cudaStreamSynchronize(h->st) != cudaSuccess) r = fail(PD_ECUDA, "product start");
             if (r == PD_OK) {
                 const HxProblem P1{g1, d0, nullptr, nullptr};
                 cudaError_t ce = hx_launch(h->B, P1, 0, h->d_v64, h->d_w64, h->d_tk, h->hxgrid[0], h->st);

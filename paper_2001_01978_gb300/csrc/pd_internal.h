@@ -495,7 +495,9 @@ cudaError_t batch_rayleigh_launch(BatchState *S, int count, int stage, cudaStrea
 // ---- learned warm start (pd_mlp.cu) ----------------------------------------------
 void mlp_features(int omega, int n, const double *e, const double *G, float *X);   // [omega x 16]
 // start vector v[s] = exp(sum_{p in s} w_p - max) on storage type dtype (synchronous)
-int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st);
+// scratch: 2^L device doubles (nullable); asynchronous on st
+int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st,
+                  double *scratch = nullptr);
 // weighted least-squares per-orbit weights of a normalised FP64 vector (synchronous)
 int product_fit(const Blocks &B, const double *v, double *w_out, cudaStream_t st);
 int mlp_predict(struct ::pairdiag_mlp *m, int omega, int n, const double *e, const double *G, double *w_out);

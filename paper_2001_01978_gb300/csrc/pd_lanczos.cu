@@ -690,65 +690,191 @@ __device__ void multisect(const R *a, const R *b2, int m, int j, R &lo, R &hi, R
     }
 }
 
-// Solve (T - theta I) z = r for a symmetric tridiagonal T by Gaussian
-// elimination with partial pivoting (row i and i+1 may swap; the upper factor
-// then has two superdiagonals).  Zero pivots are replaced by `tiny`.
-__device__ void tridiag_solve(const double *a, const double *b, int m, double theta, double *r,
-                              double *u0, double *u1, double *u2, double tiny)
+// ---- costs on GB300 that shape the code below ---------------------------------
+// A dependent FP64 FMA takes about 64 cycles and an FP64 division about 650,
+// against 4.5 and 64 for FP32.  So the small eigenproblem does its searching
+// in FP32, keeps FP64 for the final digits, spreads element-wise FP64 work
+// over the lanes, and replaces each FP64 division on a serial chain by one
+// reciprocal formed from an FP32 seed and two Newton-Raphson steps
+// r <- r + r (1 - x r) (the error squares at each step: 2^-22 -> 2^-44 -> 2^-88).
+
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    // current row i: (c0, c1, c2) in columns i, i+1, i+2
-    double c0 = a[0] - theta, c1 = (m > 1 ? b[0] : 0.0), c2 = 0.0;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 1 / x for 1e-30 <= |x| <= 1e30
+__device__ __forceinline__ double rcp64(double x)
+{
+    double r = (double)rcp_approx((float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
+// pivot magnitudes below `tiny` are raised to it (sign kept; zero -> +tiny)
+template <typename R>
+__device__ __forceinline__ R guard_pivot(R c, R tiny)
+{
+    return fabs(c) >= tiny ? c : (c < R(0) ? -tiny : tiny);
+}
+
+// Solve (T - theta I) z = r for a symmetric tridiagonal T (diagonal a, off-
+// diagonal b) by Gaussian elimination with partial pivoting (rows i and i+1 may
+// swap; the upper factor then has two superdiagonals).  One reciprocal per row
+// (rcp64 in FP64, rcp.approx in FP32); pivots below 1e-30 are raised to it.
+template <typename R>
+__device__ void tridiag_solve(const R *a, const R *b, int m, R theta, R *r, R *u0inv, R *u1, R *u2)
+{
+    const R tiny = R(1e-30);
+    R c0 = a[0] - theta, c1 = (m > 1 ? b[0] : R(0)), c2 = R(0);
     for (int i = 0; i < m - 1; ++i) {
-        // next row i+1: columns i, i+1, i+2
-        double n0 = b[i], n1 = a[i + 1] - theta, n2 = (i + 2 < m ? b[i + 1] : 0.0);
+        R n0 = b[i], n1 = a[i + 1] - theta, n2 = (i + 2 < m ? b[i + 1] : R(0));
         if (fabs(n0) > fabs(c0)) {      // swap rows i and i+1
-            double t;
+            R t;
             t = c0; c0 = n0; n0 = t;
             t = c1; c1 = n1; n1 = t;
             t = c2; c2 = n2; n2 = t;
             t = r[i]; r[i] = r[i + 1]; r[i + 1] = t;
         }
-        if (c0 == 0.0) c0 = tiny;
-        const double mu = n0 / c0;
-        u0[i] = c0; u1[i] = c1; u2[i] = c2;
+        c0 = guard_pivot<R>(c0, tiny);
+        R inv;
+        if constexpr (sizeof(R) == 8) inv = rcp64(c0);
+        else inv = rcp_approx(c0);
+        const R mu = n0 * inv;
+        u0inv[i] = inv; u1[i] = c1; u2[i] = c2;
         r[i + 1] -= mu * r[i];
         c0 = n1 - mu * c1;
         c1 = n2 - mu * c2;
-        c2 = 0.0;
+        c2 = R(0);
     }
-    if (c0 == 0.0) c0 = tiny;
-    u0[m - 1] = c0; u1[m - 1] = 0.0; u2[m - 1] = 0.0;
+    c0 = guard_pivot<R>(c0, tiny);
+    if constexpr (sizeof(R) == 8) u0inv[m - 1] = rcp64(c0);
+    else u0inv[m - 1] = rcp_approx(c0);
+    u1[m - 1] = R(0); u2[m - 1] = R(0);
     for (int i = m - 1; i >= 0; --i) {
-        double s = r[i];
-        if (i + 1 < m) s -= u1[i] * r[i + 1];
-        if (i + 2 < m) s -= u2[i] * r[i + 2];
-        r[i] = s / u0[i];
+        R t = r[i];
+        if (i + 1 < m) t -= u1[i] * r[i + 1];
+        if (i + 2 < m) t -= u2[i] * r[i + 2];
+        r[i] = t * u0inv[i];
     }
 }
 
+// z <- z / ||z|| (one lane; z first scaled by its largest magnitude, so the sum
+// of squares lies in [1, m] and an FP32 seed + two Newton steps give 1/sqrt)
+template <typename R>
+__device__ void normalise(R *z, int m)
+{
+    R big = R(0);
+    for (int i = 0; i < m; ++i) big = fmax(big, fabs(z[i]));
+    if (!(big > R(0)) || !isfinite(big)) {        // degenerate: the first unit vector
+        for (int i = 0; i < m; ++i) z[i] = i == 0 ? R(1) : R(0);
+        return;
+    }
+    R sc;
+    if constexpr (sizeof(R) == 8) sc = rcp64(big);
+    else sc = rcp_approx(big);
+    R nrm = R(0);
+    for (int i = 0; i < m; ++i) {
+        z[i] *= sc;
+        nrm += z[i] * z[i];
+    }
+    R y = (R)rsqrt_approx((float)nrm);
+    if constexpr (sizeof(R) == 8) {
+        y = y * fma(-0.5 * nrm * y, y, 1.5);
+        y = y * fma(-0.5 * nrm * y, y, 1.5);
+    }
+    for (int i = 0; i < m; ++i) z[i] *= y;
+}
+
+// Gershgorin bound of tridiag(alpha, beta) rounded up to a power of two, so
+// that scaling by it is exact in FP32 and FP64: lane k takes rows k, k+32.
+// Returns 2^e in every lane (1 for a zero matrix).
+__device__ __forceinline__ float gershgorin_pow2(const double *alpha, const double *beta, int m)
+{
+    const int lane = threadIdx.x & 31;
+    float g = 0.0f;
+    for (int k = lane; k < m; k += 32) {
+        const float rad = (k + 1 < m ? fabsf((float)beta[k]) : 0.0f) + (k > 0 ? fabsf((float)beta[k - 1]) : 0.0f);
+        g = fmaxf(g, fabsf((float)alpha[k]) + rad);
+    }
+    for (int o = 16; o > 0; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if (!(g > 0.0f) || !isfinite(g)) return 1.0f;
+    int e;
+    frexpf(g * 1.0000002f, &e);                  // g * (1 + 2 ulp) <= 2^e
+    return ldexpf(1.0f, e);
+}
+
+// p_m, p_m' and p_{m-1}, p_{m-1}' at x for the scaled matrix (diagonal a,
+// squared off-diagonal b2), p_k = (a_{k-1} - x) p_{k-1} - b2_{k-2} p_{k-2}:
+// no divisions, |p_k| <= 2.25^k.  One lane.
+struct CharPoly {
+    double pm, dpm, pm1, dpm1;
+};
+__device__ __forceinline__ CharPoly char_poly(const double *a, const double *b2, int m, double x)
+{
+    double p0 = 1.0, p1 = a[0] - x, d0 = 0.0, d1 = -1.0;
+    for (int k = 1; k < m; ++k) {
+        const double am = a[k] - x;
+        const double p2 = fma(am, p1, -b2[k - 1] * p0);
+        const double d2 = fma(am, d1, fma(-b2[k - 1], d0, -p1));
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    return CharPoly{p1, d1, p0, d0};
+}
+
+// Newton steps x <- x - p_m(x) / p_m'(x) for the lowest eigenvalue from the
+// midpoint of an FP32 bracket [lo, hi] (one lane).  `evals` evaluations; cp
+// holds the last one (at the returned x, before its own step).  False when a
+// step leaves the bracket widened by 1e-6 or a value is not finite.
+__device__ bool newton_lowest(const double *a, const double *b2, int m, float lo, float hi, int evals, double &x,
+                              CharPoly &cp)
+{
+    const double wlo = (double)lo - 1e-6, whi = (double)hi + 1e-6;
+    x = 0.5 * ((double)lo + (double)hi);
+    for (int it = 0; it < evals; ++it) {
+        cp = char_poly(a, b2, m, x);
+        if (!(fabs(cp.dpm) >= 1e-30 && fabs(cp.dpm) <= 1e30) || !isfinite(cp.pm)) return false;
+        if (it + 1 == evals) return true;
+        const double xn = x - cp.pm * rcp64(cp.dpm);
+        if (!(xn >= wlo && xn <= whi)) return false;
+        x = xn;
+    }
+    return true;
+}
+
 // Lowest two eigenvalues and the lowest eigenvector of the m x m symmetric
-// tridiagonal matrix (alpha, beta), computed by one warp.  The work arrays live
-// in shared memory (kMaxWindow doubles each).
+// tridiagonal matrix (alpha, beta), computed by one warp.  Work arrays in
+// shared memory (kMaxWindow doubles each).  Steps: exact power-of-two scaling;
+// FP32 multisection brackets of the two lowest eigenvalues; Newton steps on the
+// characteristic polynomial in FP64 for the lowest (FP64 multisection if they
+// leave the bracket); two FP32 inverse iterations, then one in FP64 at the
+// refined eigenvalue, for its eigenvector.
 __device__ void tridiag_warp(const double *alpha, const double *beta, int m, double *theta_out, double *s_out,
                              double *a, double *b, double *b2, double *z, double *u0, double *u1, double *u2)
 {
     const int lane = threadIdx.x & 31;
-    // Gershgorin scale of T (each lane computes it; m <= 64)
-    double scale = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const double rad = (i + 1 < m ? fabs(beta[i]) : 0.0) + (i > 0 ? fabs(beta[i - 1]) : 0.0);
-        scale = fmax(scale, fabs(alpha[i]) + rad);
-    }
-    if (!(scale > 0.0)) scale = 1.0;
-    const double inv = 1.0 / scale;
-    // scaled copies: a, b, b2 (double) and their FP32 twins in u0/u1 storage
+    const float scf = gershgorin_pow2(alpha, beta, m);
+    const double scale = (double)scf, inv = 1.0 / (double)scf;      // exact powers of two
     float *af = reinterpret_cast<float *>(u0);
+    float *bf = af + kMaxWindow;
     float *b2f = reinterpret_cast<float *>(u1);
+    float *zf = b2f + kMaxWindow;
     for (int i = lane; i < m; i += 32) {
         a[i] = alpha[i] * inv;
         b[i] = (i + 1 < m) ? beta[i] * inv : 0.0;
         b2[i] = b[i] * b[i];
         af[i] = (float)a[i];
+        bf[i] = (float)b[i];
         b2f[i] = (float)b2[i];
     }
     __syncwarp();
@@ -761,25 +887,45 @@ __device__ void tridiag_warp(const double *alpha, const double *beta, int m, dou
     float lo1 = -1.25f, hi1 = 1.25f, lo2 = -1.25f, hi2 = 1.25f;
     multisect<float>(af, b2f, m, 1, lo1, hi1, 4e-7f);
     multisect<float>(af, b2f, m, 2, lo2, hi2, 4e-7f);
-    // FP64 refinement of the lowest from its (slightly widened) FP32 bracket
-    double lo = (double)lo1 - 1e-6, hi = (double)hi1 + 1e-6;
-    if (sturm_count<double>(a, b2, m, lo) >= 1) lo = -1.25;      // the widened bracket must hold it
-    if (sturm_count<double>(a, b2, m, hi) < 1) hi = 1.25;
-    multisect<double>(a, b2, m, 1, lo, hi, 2.0 * DBL_EPSILON);
-    const double t1 = 0.5 * (lo + hi);
+    const double wlo = (double)lo1 - 1e-6, whi = (double)hi1 + 1e-6;
+    // three Newton steps in FP64 from the FP32 bracket (the error squares each
+    // step: 4e-7 -> 1e-13 -> 1e-26), the last step taken from the last evaluation
+    int ok = 0;
+    double t1 = 0.0;
+    if (lane == 0) {
+        CharPoly cp;
+        ok = newton_lowest(a, b2, m, lo1, hi1, 3, t1, cp);
+        if (ok) {
+            const double xn = t1 - cp.pm * rcp64(cp.dpm);
+            ok = xn >= wlo && xn <= whi;
+            t1 = xn;
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    t1 = __shfl_sync(0xffffffffu, t1, 0);
+    if (!ok) {                                     // FP64 multisection from the widened bracket
+        double lo = wlo, hi = whi;
+        if (sturm_count<double>(a, b2, m, lo) >= 1) lo = -1.25;
+        if (sturm_count<double>(a, b2, m, hi) < 1) hi = 1.25;
+        multisect<double>(a, b2, m, 1, lo, hi, 2.0 * DBL_EPSILON);
+        t1 = 0.5 * (lo + hi);
+    }
     const double t2 = 0.5 * ((double)lo2 + (double)hi2);
     __syncwarp();
     if (lane == 0) {
-        // inverse iteration for the eigenvector of t1 (scaled matrix)
-        const double tiny = DBL_EPSILON;
-        for (int i = 0; i < m; ++i) z[i] = 1.0;
+        // eigenvector: two FP32 inverse iterations from (1, ..., 1) at the FP32
+        // eigenvalue, then one FP64 iteration at the refined one
+        const float t1f = (float)t1;
+        float *u0f = reinterpret_cast<float *>(u2), *u1f = u0f + kMaxWindow;
+        float *u2f = reinterpret_cast<float *>(b2) ;   // b2 is no longer needed
+        for (int i = 0; i < m; ++i) zf[i] = 1.0f;
         for (int it = 0; it < 2; ++it) {
-            tridiag_solve(a, b, m, t1, z, u0, u1, u2, tiny);
-            double nrm = 0.0;
-            for (int i = 0; i < m; ++i) nrm += z[i] * z[i];
-            nrm = 1.0 / sqrt(nrm);
-            for (int i = 0; i < m; ++i) z[i] *= nrm;
+            tridiag_solve<float>(af, bf, m, t1f, zf, u0f, u1f, u2f);
+            normalise<float>(zf, m);
         }
+        for (int i = 0; i < m; ++i) z[i] = (double)zf[i];
+        tridiag_solve<double>(a, b, m, t1, z, u0, u1, u2);
+        normalise<double>(z, m);
         double big = 0.0; int ib = 0;                 // fix the sign: largest component positive
         for (int i = 0; i < m; ++i) if (fabs(z[i]) > big) { big = fabs(z[i]); ib = i; }
         const double sg = z[ib] < 0.0 ? -1.0 : 1.0;
@@ -791,29 +937,29 @@ __device__ void tridiag_warp(const double *alpha, const double *beta, int m, dou
 }
 
 // Residual test of the lowest Ritz pair of a cycle so far (steps 0..i).  With
-// full reorthogonalisation the residual equals beta_i |s_last|, s the lowest
-// eigenvector of the (i+1) x (i+1) matrix tridiag(alpha, beta) (Algorithm 2),
-// taken here from an FP32 multisection and two inverse-iteration solves.
-// Returns, in every lane, whether it is within tol of |theta|.  One warp; the
-// work arrays (kMaxWindow doubles each) are shared memory of this warp.
+// full reorthogonalisation the residual equals beta_i |s_m| (m = i + 1), s the
+// lowest eigenvector of tridiag(alpha, beta) (Algorithm 2).  No eigenvector is
+// formed: with p_k the characteristic polynomials of the leading k x k blocks
+// (of T - x I), s_m^2 = -p_{m-1}(theta) / p_m'(theta).  theta comes from an FP32
+// multisection and two FP64 Newton steps; at the last point x the first-order
+// correction p_{m-1}(theta) ~ p_{m-1}(x) - (p_m(x) / p_m'(x)) p_{m-1}'(x)
+// removes the error of x, so tiny |s_m| (a converged pair) are resolved.
+// Returns, in every lane, whether beta_i |s_m| <= tol |theta|; a failed Newton
+// step or a negative or non-finite s_m^2 counts as not converged.  One warp;
+// work arrays as for tridiag_warp.
 __device__ bool ritz_converged_warp(const double *alpha, const double *beta, int i, double tol, double *a,
                                     double *b, double *b2, double *z, double *u0, double *u1, double *u2)
 {
     const int m = i + 1;
     const int lane = threadIdx.x & 31;
-    double scale = 0.0;
-    for (int k = 0; k < m; ++k) {
-        const double rad = (k + 1 < m ? fabs(beta[k]) : 0.0) + (k > 0 ? fabs(beta[k - 1]) : 0.0);
-        scale = fmax(scale, fabs(alpha[k]) + rad);
-    }
-    if (!(scale > 0.0)) return false;
-    const double inv = 1.0 / scale;
+    const float scf = gershgorin_pow2(alpha, beta, m);
+    const double inv = 1.0 / (double)scf;          // exact: a power of two
     float *af = reinterpret_cast<float *>(u0);
     float *b2f = reinterpret_cast<float *>(u1);
     for (int k = lane; k < m; k += 32) {
         a[k] = alpha[k] * inv;
-        b[k] = (k + 1 < m) ? beta[k] * inv : 0.0;
-        b2[k] = b[k] * b[k];
+        const double bk = (k + 1 < m) ? beta[k] * inv : 0.0;
+        b2[k] = bk * bk;
         af[k] = (float)a[k];
         b2f[k] = (float)b2[k];
     }
@@ -823,17 +969,16 @@ __device__ bool ritz_converged_warp(const double *alpha, const double *beta, int
     __syncwarp();
     int ok = 0;
     if (lane == 0) {
-        const double t = 0.5 * ((double)lo + (double)hi);
-        for (int k = 0; k < m; ++k) z[k] = 1.0;
-        for (int it = 0; it < 2; ++it) {
-            tridiag_solve(a, b, m, t, z, u0, u1, u2, DBL_EPSILON);
-            double nrm = 0.0;
-            for (int k = 0; k < m; ++k) nrm += z[k] * z[k];
-            nrm = 1.0 / sqrt(nrm);
-            for (int k = 0; k < m; ++k) z[k] *= nrm;
+        double x;
+        CharPoly cp;
+        if (newton_lowest(a, b2, m, lo, hi, 3, x, cp)) {
+            const double rd = rcp64(cp.dpm);
+            const double pm1 = cp.pm1 - cp.pm * rd * cp.dpm1;      // p_{m-1} at the refined eigenvalue
+            const double s2 = -pm1 * rd;
+            const double th = fabs(x - cp.pm * rd) * (double)scf;
+            const double bi = beta[i];
+            ok = s2 >= 0.0 && isfinite(s2) && isfinite(bi) && bi * bi * s2 <= (tol * th) * (tol * th);
         }
-        const double r = beta[i] * fabs(z[m - 1]);
-        ok = isfinite(r) && r <= tol * fabs(t * scale);
     }
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }

@@ -491,6 +491,55 @@ product_start_kernel(const Blocks B, const OrbitWeights w, double shift, T *__re
     }
 }
 
+// The same vector as a product of two factors, exp(sum over the state's high
+// orbits - shift) * exp(sum over its low orbits): the low factor of every L-bit
+// low word is tabulated once (elow, in the order of the lowword table), the
+// high factor once per block, so a state costs one multiply instead of an
+// FP64 exponential (GB300 executes FP64 at a small fraction of its FP32 rate).
+__global__ void __launch_bounds__(256)
+low_factor_kernel(const Blocks B, const OrbitWeights w, double *__restrict__ elow)
+{
+    const int nw = 1 << B.L;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (uint32_t m = B.lowword[t]; m; m &= m - 1) s += w.w[__ffs(m) - 1];
+        elow[t] = exp(s);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+product_factored_kernel(const Blocks B, const OrbitWeights w, double shift, const double *__restrict__ elow,
+                        T *__restrict__ v)
+{
+    __shared__ double s_high;
+    for (long long b = blockIdx.x; b < B.nblocks; b += gridDim.x) {
+        const uint64_t h = B.blk_h[b], base = B.blk_base[b];
+        const int k = B.n - __popcll(h);
+        const int nk = (int)B.binom[B.L * kBinomStride + k];
+        int off = 0;
+        for (int j = 0; j < k; ++j) off += (int)B.binom[B.L * kBinomStride + j];
+        __syncthreads();                          // s_high of the previous block is consumed
+        if (threadIdx.x == 0) {
+            double sh = -shift;
+            for (uint64_t m = h; m; m &= m - 1) sh += w.w[B.L + __ffsll((long long)m) - 1];
+            s_high = exp(sh);
+        }
+        __syncthreads();
+        const double eh = s_high;
+        const double *el = elow + off;
+        for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+            const T x = (T)(eh * el[r]);
+            if (B.kept_map) {                     // truncated space: kept states only
+                const int32_t m = B.kept_map[base + r];
+                if (m >= 0) v[m] = x;
+            } else {
+                v[base + r] = x;
+            }
+        }
+    }
+}
+
 // per CTA: M[i][j] += psi^2 n_i n_j, b[i] += psi^2 n_i log|psi| (shared accumulators)
 __global__ void __launch_bounds__(256)
 fit_kernel(const Blocks B, const double *__restrict__ v, double *__restrict__ part)
@@ -664,8 +713,10 @@ void mlp_features(int omega, int n, const double *e, const double *G, float *X)
     }
 }
 
-// weights w (host, [omega]) -> start vector (device) of storage dtype
-int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st)
+// weights w (host, [omega]) -> start vector (device) of storage dtype.
+// scratch: 2^L device doubles for the low-word factors (nullable: then one
+// FP64 exponential per state).  Asynchronous on st.
+int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cudaStream_t st, double *scratch)
 {
     std::vector<double> w(w_host, w_host + B.omega);
     std::vector<double> srt(w);
@@ -674,12 +725,22 @@ int product_start(const Blocks &B, const double *w_host, int dtype, void *v, cud
     for (int i = 0; i < B.n; ++i) shift += srt[i];        // the largest exponent over the basis
     OrbitWeights ow{};
     for (int p = 0; p < B.omega; ++p) ow.w[p] = w[p];
+    // the factors stay finite when neither partial exponent can pass 700
+    double lo_abs = 0.0, hi_abs = std::fabs(shift);
+    for (int p = 0; p < B.omega; ++p) (p < B.L ? lo_abs : hi_abs) += std::fabs(w[p]);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.nblocks, sm_count() * 4));
-    if (dtype == 0) product_start_kernel<double><<<grid, 256, 0, st>>>(B, ow, shift, (double *)v);
-    else product_start_kernel<float><<<grid, 256, 0, st>>>(B, ow, shift, (float *)v);
-    count_launches(1);
+    if (scratch && lo_abs < 700.0 && hi_abs < 700.0) {
+        const int tgrid = ((1 << B.L) + 255) / 256;
+        low_factor_kernel<<<tgrid, 256, 0, st>>>(B, ow, scratch);
+        if (dtype == 0) product_factored_kernel<double><<<grid, 256, 0, st>>>(B, ow, shift, scratch, (double *)v);
+        else product_factored_kernel<float><<<grid, 256, 0, st>>>(B, ow, shift, scratch, (float *)v);
+        count_launches(2);
+    } else {
+        if (dtype == 0) product_start_kernel<double><<<grid, 256, 0, st>>>(B, ow, shift, (double *)v);
+        else product_start_kernel<float><<<grid, 256, 0, st>>>(B, ow, shift, (float *)v);
+        count_launches(1);
+    }
     PD_CUDA(cudaGetLastError());
-    PD_CUDA(cudaStreamSynchronize(st));
     return PD_OK;
 }
 
