@@ -304,7 +304,7 @@ def run_ours(args):
 
     # ---- timed region: K mixed solves ----
     pd.pairdiag_set_profiling(mixed.h, True)
-    pd.pairdiag_get_profile(mixed.h)          # clear
+    pd.pairdiag_get_profile(mixed.h, -1)      # clear
     clocks = ClockSampler(local)
     launches0 = pd.pairdiag_kernel_launches()
     barrier()
@@ -326,6 +326,7 @@ def run_ours(args):
     launches = pd.pairdiag_kernel_launches() - launches0
     clk = clocks.stop()
     hx_count, hx_ms = pd.pairdiag_get_profile(mixed.h)
+    hx64_count, hx64_ms = pd.pairdiag_get_profile(mixed.h, pd.PD_PREC_FP64)   # the FP64 refinement products
     pd.pairdiag_set_profiling(mixed.h, False)
 
     total_ms = sum(step_ms)
@@ -414,7 +415,9 @@ def run_ours(args):
                 "traffic": traffic, "achieved_is": "algorithmic bytes / time (effective)",
                 "dram_gbs": (traffic / avg_hx_s / 1e9) if traffic else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_hx_s * 1e3,
-                "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": hx_ms / total_ms,
+                "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": (hx_ms + hx64_ms) / total_ms,
+                "hx32_share_of_step": hx_ms / total_ms,
+                "hx_share_is": "all H*x products of a solve (FP32 cycles + FP64 refinement) / solve time",
                 "timed_launches": hx_count, "executed_products": hx_executed}
 
     cpu = None
@@ -588,7 +591,7 @@ def forms_on(args, workload, ws, steps, warmup, kato_temple=False):
                 flush.fill_(1.0)
                 pd.pairdiag_ground_state_dev(s.h, args.tol, None)
             pd.pairdiag_set_profiling(s.h, True)
-            pd.pairdiag_get_profile(s.h)                  # clear
+            pd.pairdiag_get_profile(s.h, -1)              # clear
             times, r, executed = [], None, 0
             v = torch.empty(dim, dtype=torch.float64, device="cuda") if kato_temple else None
             for i in range(max(1, steps)):

@@ -470,8 +470,9 @@ int64_t pairdiag_kernel_launches(void);
  * Kernel timing of the handle's H*x launches: while enabled (on != 0), every
  * H*x launch of the handle is bracketed by CUDA events on the handle's stream.
  * pairdiag_get_profile synchronises the stream, returns the number of timed
- * launches of the given precision (PD_PREC_FP64 or PD_PREC_MIXED = FP32) and
- * their summed duration in milliseconds, and clears the whole record.
+ * launches of the given precision (PD_PREC_FP64 or PD_PREC_MIXED = FP32; a
+ * negative precision: all of them) and their summed duration in milliseconds,
+ * and clears the records it returned (those of the other precision stay).
  */
 int pairdiag_set_profiling(pairdiag_t *h, int on);
 int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms);

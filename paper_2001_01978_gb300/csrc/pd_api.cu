@@ -845,8 +845,14 @@ int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, dou
     PD_CUDA(cudaStreamSynchronize(h->st));
     double total = 0.0;
     int64_t count = 0;
+    size_t kept = 0;                              // records of other precisions stay, in order
     for (size_t i = 0; i < h->hx_events_used; ++i) {
-        if (h->hx_event_prec[i] != precision) continue;
+        if (precision >= 0 && h->hx_event_prec[i] != precision) {
+            std::swap(h->hx_events[kept], h->hx_events[i]);
+            std::swap(h->hx_event_prec[kept], h->hx_event_prec[i]);
+            ++kept;
+            continue;
+        }
         float ms = 0.0f;
         PD_CUDA(cudaEventElapsedTime(&ms, h->hx_events[i].first, h->hx_events[i].second));
         total += ms;
@@ -854,7 +860,7 @@ int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, dou
     }
     *hx_launches = count;
     *hx_ms = total;
-    h->hx_events_used = 0;
+    h->hx_events_used = kept;
     return PD_OK;
 }
 

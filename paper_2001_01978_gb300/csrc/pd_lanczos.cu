@@ -135,8 +135,10 @@ __device__ __forceinline__ void finalize_step(LanczosScalars *S, int i, double n
     if (!(b > 1e-13 * tn)) S->broken = 1;
 }
 
-// out[j] = Q_j^T p for j < m (partials per CTA; with a ticket the last CTA adds them)
-template <typename T, int W>
+// out[j] = Q_j^T p for j < m (partials per CTA; with a ticket the last CTA adds
+// them).  NG vectors per pass: 1 for a single dot, so that no predicated-off
+// multiply-adds are issued (FP64 ones occupy GB300's small FP64 pipe).
+template <typename T, int W, int NG = kGroup>
 __global__ void __launch_bounds__(kThreads)
 dots_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p, int64_t n,
             double *__restrict__ part, double *__restrict__ out, unsigned long long *ticket,
@@ -147,21 +149,21 @@ dots_kernel(const T *__restrict__ Q, int64_t ldq, int m, const T *__restrict__ p
     const int64_t nc = (n + W - 1) / W;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t c0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    for (int j0 = 0; j0 < m; j0 += kGroup) {
+    for (int j0 = 0; j0 < m; j0 += NG) {
         DotAcc<T> acc[kGroup];
         for (int64_t c = c0; c < nc; c += stride) {
             const Pack<T, W> pv = load_pack<T, W, true>(p, c, n);
             Pack<T, W> q[kGroup];
 #pragma unroll
-            for (int u = 0; u < kGroup; ++u)
+            for (int u = 0; u < NG; ++u)
                 if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
 #pragma unroll
-            for (int u = 0; u < kGroup; ++u)
+            for (int u = 0; u < NG; ++u)
                 if (j0 + u < m)
 #pragma unroll
                     for (int k = 0; k < W; ++k) acc[u].add(q[u].v[k], pv.v[k]);
         }
-        block_reduce_group<T>(acc, min(kGroup, m - j0), shg, part + (int64_t)blockIdx.x * kMaxWindow + j0);
+        block_reduce_group<T>(acc, min(NG, m - j0), shg, part + (int64_t)blockIdx.x * kMaxWindow + j0);
     }
     if (ticket && arrive_last(ticket)) reduce_partials(part, gridDim.x, m, out);
 }
@@ -420,20 +422,22 @@ __device__ __forceinline__ bool grid_sync(GridBar *gb, int *s_ok)
     return *s_ok != 0;
 }
 
-// the packs c of the group's vectors Q_j0 .. Q_{j0+kGroup-1} that exist (j < m)
-template <typename T, int W>
-__device__ __forceinline__ void load_group(Pack<T, W> (&q)[kGroup], const T *__restrict__ Q, int64_t ldq, int j0,
+// the packs c of the group's vectors Q_j0 .. Q_{j0+KG-1} that exist (j < m)
+template <typename T, int W, int KG>
+__device__ __forceinline__ void load_group(Pack<T, W> (&q)[KG], const T *__restrict__ Q, int64_t ldq, int j0,
                                            int m, int64_t c, int64_t n)
 {
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u)
-        if (j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
+    for (int u = 0; u < KG; ++u)
+        if (KG == 1 || j0 + u < m) q[u] = load_pack<T, W, true>(Q + (int64_t)(j0 + u) * ldq, c, n);
 }
 
 // Ownership: the packs form chunks of kStepThreads; CTA b owns the K
 // consecutive chunks b*K .. b*K + K - 1, thread t pack t of each.  Local pack
 // slot (chunk l of the CTA, thread t) = l * kStepThreads + t.
-template <typename T, int W, bool SMEM>
+// KG: vectors per group pass (1, 2, 4 or 8, chosen per launch so that the
+// last group issues few predicated-off multiply-adds)
+template <typename T, int W, bool SMEM, int KG>
 __global__ void __launch_bounds__(kStepThreads, 1)
 step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p, int64_t n,
             typename StepRed<T>::P *part, GridBar *gb, T *qnext)
@@ -470,31 +474,31 @@ step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p
     const int64_t K = (nchunk + G - 1) / G;
     const int64_t first = (int64_t)blockIdx.x * K;
     const int64_t mine = first < nchunk ? (nchunk - first < K ? nchunk - first : K) : 0;   // chunks of this CTA
-    const int ng = (m + kGroup - 1) / kGroup;
+    const int ng = (m + KG - 1) / KG;
     auto pack_of = [&](int64_t l) { return (first + l) * kStepThreads + tid; };
 
     // phase 1: p <- p - alpha q_i - beta_{i-1} q_{i-1}; c_j = Q_j^T p (j <= i).
     // Two chunks per iteration, all their loads issued before the first use.
     for (int g = 0; g < ng; ++g) {
-        const int j0 = g * kGroup;
-        PackAcc<T> acc[kGroup];
+        const int j0 = g * KG;
+        PackAcc<T> acc[KG];
         for (int64_t l = 0; l < mine; l += 2) {
             const int64_t c0 = pack_of(l), c1 = pack_of(l + 1);
             const bool ok0 = c0 < nc, ok1 = l + 1 < mine && c1 < nc;
-            Pack<T, W> v[2], q[2][kGroup];
+            Pack<T, W> v[2], q[2][KG];
             if (g == 0) {
                 Pack<T, W> x[2], y[2];
                 if (ok0) {
                     v[0] = load_pack<T, W, false>(p, c0, n);
                     x[0] = load_pack<T, W, true>(qi, c0, n);
                     y[0] = load_pack<T, W, true>(qm, c0, n);
-                    load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+                    load_group<T, W, KG>(q[0], Q, ldq, j0, m, c0, n);
                 }
                 if (ok1) {
                     v[1] = load_pack<T, W, false>(p, c1, n);
                     x[1] = load_pack<T, W, true>(qi, c1, n);
                     y[1] = load_pack<T, W, true>(qm, c1, n);
-                    load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+                    load_group<T, W, KG>(q[1], Q, ldq, j0, m, c1, n);
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -508,26 +512,26 @@ step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p
             } else {
                 if (ok0) {
                     v[0] = SMEM ? sv[l * kStepThreads + tid] : load_pack<T, W, false>(p, c0, n);
-                    load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+                    load_group<T, W, KG>(q[0], Q, ldq, j0, m, c0, n);
                 }
                 if (ok1) {
                     v[1] = SMEM ? sv[(l + 1) * kStepThreads + tid] : load_pack<T, W, false>(p, c1, n);
-                    load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+                    load_group<T, W, KG>(q[1], Q, ldq, j0, m, c1, n);
                 }
             }
             if (ok0) {
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
+                for (int u = 0; u < KG; ++u)
                     if (j0 + u < m) acc[u].add(q[0][u], v[0]);
             }
             if (ok1) {
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
+                for (int u = 0; u < KG; ++u)
                     if (j0 + u < m) acc[u].add(q[1][u], v[1]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u)
+        for (int u = 0; u < KG; ++u)
             if (j0 + u < m) {
                 const P s = warp_allsum<R>(R::from(acc[u]));
                 if (lane == 0) wpart[w][j0 + u] = s;
@@ -557,27 +561,27 @@ step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p
     // read last are the likeliest still in L2), then ||p||^2
     PackAcc<T> nrm;
     for (int g = ng - 1; g >= 0; --g) {
-        const int j0 = g * kGroup;
-        T cg[kGroup];
+        const int j0 = g * KG;
+        T cg[KG];
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) cg[u] = (j0 + u < m) ? scT[j0 + u] : T(0);
+        for (int u = 0; u < KG; ++u) cg[u] = (j0 + u < m) ? scT[j0 + u] : T(0);
         for (int64_t l = 0; l < mine; l += 2) {
             const int64_t c0 = pack_of(l), c1 = pack_of(l + 1);
             const bool ok0 = c0 < nc, ok1 = l + 1 < mine && c1 < nc;
-            Pack<T, W> v[2], q[2][kGroup];
+            Pack<T, W> v[2], q[2][KG];
             if (ok0) {
                 v[0] = SMEM ? sv[l * kStepThreads + tid] : load_pack<T, W, false>(p, c0, n);
-                load_group<T, W>(q[0], Q, ldq, j0, m, c0, n);
+                load_group<T, W, KG>(q[0], Q, ldq, j0, m, c0, n);
             }
             if (ok1) {
                 v[1] = SMEM ? sv[(l + 1) * kStepThreads + tid] : load_pack<T, W, false>(p, c1, n);
-                load_group<T, W>(q[1], Q, ldq, j0, m, c1, n);
+                load_group<T, W, KG>(q[1], Q, ldq, j0, m, c1, n);
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!(h == 0 ? ok0 : ok1)) continue;
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
+                for (int u = 0; u < KG; ++u)
                     if (j0 + u < m)
 #pragma unroll
                         for (int k = 0; k < W; ++k) v[h].v[k] = fma_t<T>(-cg[u], q[h][u].v[k], v[h].v[k]);
@@ -1549,8 +1553,14 @@ void dots_t(const T *Q, int64_t ld, int m, const T *p, int64_t n, double *part, 
     constexpr int W = kPackBytes / sizeof(T);
     const bool pk = packable<T>({Q, p}, ld);
     const int g = pk ? wave_grid<dots_kernel<T, W>>(pack_units<T>(n, pk)) : wave_grid<dots_kernel<T, 1>>(n);
-    if (pk) dots_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
-    else dots_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    if (m == 1) {
+        if (pk) dots_kernel<T, W, 1><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+        else dots_kernel<T, 1, 1><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    } else if (pk) {
+        dots_kernel<T, W><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    } else {
+        dots_kernel<T, 1><<<g, kThreads, 0, st>>>(Q, ld, m, p, n, part, out, ticket, skip);
+    }
     count_launches(1);
     if (!ticket) reduce(part, g, m, out, st, skip);
 }
@@ -1608,13 +1618,58 @@ void ritz_t(T *Q, int64_t ld, const int *m_dev, const double *s, int64_t n, doub
     if (!ticket) reduce(part, g, 1, norm_out, st);
 }
 
-// the step kernel instance of a plan
-template <typename T>
-const void *step_fn(bool packed, bool in_smem)
+// the step kernel instance of a plan and a group size
+template <typename T, int KG>
+const void *step_fn_kg(bool packed, bool in_smem)
 {
     constexpr int W = kPackBytes / sizeof(T);
-    if (packed) return in_smem ? (const void *)step_kernel<T, W, true> : (const void *)step_kernel<T, W, false>;
-    return in_smem ? (const void *)step_kernel<T, 1, true> : (const void *)step_kernel<T, 1, false>;
+    if (packed)
+        return in_smem ? (const void *)step_kernel<T, W, true, KG> : (const void *)step_kernel<T, W, false, KG>;
+    return in_smem ? (const void *)step_kernel<T, 1, true, KG> : (const void *)step_kernel<T, 1, false, KG>;
+}
+
+template <typename T>
+const void *step_fn(bool packed, bool in_smem, int kg)
+{
+    return kg <= 1   ? step_fn_kg<T, 1>(packed, in_smem)
+           : kg <= 2 ? step_fn_kg<T, 2>(packed, in_smem)
+           : kg <= 4 ? step_fn_kg<T, 4>(packed, in_smem)
+                     : step_fn_kg<T, 8>(packed, in_smem);
+}
+
+// Group size for a step with m vectors in the window.  FP32: the fewest passes
+// (8, or the power of two >= m).  FP64, whose multiply-adds occupy GB300's
+// small FP64 pipe even when predicated off: the largest of 8, 4, 2, 1 whose
+// last group leaves at most one vector slot idle.
+template <typename T>
+int step_group(int m)
+{
+    if (sizeof(T) == 4) return m >= 8 ? 8 : m > 2 ? 4 : m;
+    for (int kg = 8; kg > 1; kg >>= 1)
+        if ((kg - m % kg) % kg <= 1) return kg;
+    return 1;
+}
+
+// the resident CTAs per SM of every group-size instance (the smallest)
+template <typename T>
+int step_per_sm(bool packed, bool in_smem, size_t smem)
+{
+    int lo = 1 << 30;
+    for (int kg = 1; kg <= kGroup; kg <<= 1) {
+        const void *fn = step_fn<T>(packed, in_smem, kg);
+        if (in_smem && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, in_smem ? smem : 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        lo = std::min(lo, per_sm);
+    }
+    return lo;
 }
 
 template <typename T>
@@ -1641,25 +1696,11 @@ int step_plan_t(int64_t n, int64_t ldq, const void *Q, const void *p, StepPlan *
     int64_t slice = (nchunk + grid - 1) / grid * kStepThreads;      // packs per CTA, whole chunks
     const size_t smem = (size_t)slice * step_pack_bytes<T>(pk);
     bool in_smem = smem <= kStepSmemMax;
-    const void *fn = step_fn<T>(pk, in_smem);
-    if (in_smem && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
+    int per_sm = in_smem ? step_per_sm<T>(pk, true, smem) : 0;
+    if (per_sm < 1 || grid > (int64_t)per_sm * sm_count()) {   // without the slice in shared memory
         in_smem = false;
-        fn = step_fn<T>(pk, false);
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, in_smem ? smem : 0) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (grid > (int64_t)per_sm * sm_count()) {     // fewer CTAs resident than planned: without the slice in shared memory
-        in_smem = false;
-        fn = step_fn<T>(pk, false);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, 0) != cudaSuccess || per_sm < 1) {
-            cudaGetLastError();
-            return 0;
-        }
+        per_sm = step_per_sm<T>(pk, false, 0);
+        if (per_sm < 1) return 0;
         grid = std::min<int64_t>(grid, (int64_t)per_sm * sm_count());
         slice = (nchunk + grid - 1) / grid * kStepThreads;
     }
@@ -1679,7 +1720,7 @@ cudaError_t step_t(const StepPlan &plan, const T *Q, int64_t ldq, int i, Lanczos
     P *pp = reinterpret_cast<P *>(part);
     void *args[] = {(void *)&Q, (void *)&ldq, (void *)&i, (void *)&S, (void *)&p, (void *)&n, (void *)&pp,
                     (void *)&gb, (void *)&qnext};
-    const void *fn = step_fn<T>(plan.packed, plan.in_smem);
+    const void *fn = step_fn<T>(plan.packed, plan.in_smem, step_group<T>(i + 1));
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(kStepThreads), args, plan.smem, st);
     count_launches(1);
     return e;

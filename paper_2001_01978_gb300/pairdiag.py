@@ -468,7 +468,7 @@ def pairdiag_set_step_fusion(h, on: bool) -> None:
 
 def pairdiag_get_profile(h, precision: int = PD_PREC_MIXED):
     """(number of timed H*x launches of this precision, their summed duration in
-    ms); clears the whole record."""
+    ms); clears the records returned (precision < 0: all precisions)."""
     n = ctypes.c_int64()
     ms = ctypes.c_double()
     _check(lib().pairdiag_get_profile(h, precision, ctypes.byref(n), ctypes.byref(ms)))
