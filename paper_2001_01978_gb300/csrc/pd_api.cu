@@ -470,7 +470,11 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
     std::vector<double> history;                  // |beta_1/alpha_1| per cycle
     bool ended_early = false;                     // the last cycle stopped before the full window
     double est_tol = tol;                         // threshold of the Ritz estimate
-    for (int cycle = 0; cycle <= max_cycles; ++cycle) {
+    // One synchronisation per cycle: the end of a cycle (its Ritz values) and
+    // step 0 of the next (the restart test) are read back together.
+    double ab[2] = {0.0, 0.0}, th[2] = {0.0, 0.0};
+    int used = 0, berr = 0;
+    auto begin_cycle = [&]() -> int {
         if (h->n_locked) {                        // restart vector orthogonal to the locked states
             PD_TRY(lock_project(h, dtype, Q, nullptr));
             PD_CUDA(multidot_launch(dtype, Q, h->ldq, 1, Q, dim, h->d_part, &S->dots[0], st, nullptr, tk));
@@ -478,13 +482,29 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         }
         PD_CUDA(cycle_reset_launch(S, st));
         PD_TRY(lanczos_step(h, dtype, 0, m));
-        double ab[2];
         PD_CUDA(cudaMemcpyAsync(&ab[0], &S->alpha[0], sizeof(double), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaMemcpyAsync(&ab[1], &S->beta[0], sizeof(double), cudaMemcpyDeviceToHost, st));
-        int berr = 0;
         PD_CUDA(cudaMemcpyAsync(&berr, &h->d_tk->bar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        return PD_OK;
+    };
+    auto end_cycle = [&](int cycle) -> int {     // after the synchronisation
+        cs.iterations += used - 1;
+        ended_early = used < m;
+        if (!std::isfinite(th[0])) return fail(PD_ECUDA, "non-finite Ritz value in cycle %d", cycle);
+        cs.energy = th[0];
+        cs.gap = th[1] - th[0];
+        return PD_OK;
+    };
+    PD_TRY(begin_cycle());
+    bool pending = false;                         // the previous cycle's end is still to be read
+    for (int cycle = 0; cycle <= max_cycles; ++cycle) {
         PD_CUDA(cudaStreamSynchronize(st));
         PD_TRY(check_barrier(h, berr));
+        if (pending) {
+            PD_TRY(end_cycle(cycle - 1));
+            ++cs.restarts;
+            pending = false;
+        }
         ++cs.iterations;
         if (!std::isfinite(ab[0]) || !std::isfinite(ab[1]))
             return fail(PD_ECUDA, "non-finite Lanczos coefficient in cycle %d", cycle);
@@ -517,23 +537,18 @@ int run_cycles(pairdiag *h, int dtype, double tol, int max_cycles, CycleStats &c
         PD_CUDA(tridiag_launch(S, 0, st));
         PD_CUDA(ritz_launch(dtype, Q, h->ldq, &S->used, S->s, dim, h->d_part, &S->norm2, st, tk));
         PD_CUDA(scale_launch(dtype, Q, Q, dim, &S->norm2, 1, st));
-        double th[2];
-        int used = 0;
         PD_CUDA(cudaMemcpyAsync(th, S->theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaMemcpyAsync(&used, &S->used, sizeof(int), cudaMemcpyDeviceToHost, st));
         PD_CUDA(cudaMemcpyAsync(&berr, &h->d_tk->bar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        PD_CUDA(cudaStreamSynchronize(st));
-        PD_TRY(check_barrier(h, berr));
-        cs.iterations += used - 1;
-        ended_early = used < m;
-        if (!std::isfinite(th[0])) return fail(PD_ECUDA, "non-finite Ritz value in cycle %d", cycle);
-        cs.energy = th[0];
-        cs.gap = th[1] - th[0];
-        if (h->opt.mode == 1) {
-            cs.converged = true;
+        if (h->opt.mode == 1 || cycle == max_cycles) {   // no next cycle
+            PD_CUDA(cudaStreamSynchronize(st));
+            PD_TRY(check_barrier(h, berr));
+            PD_TRY(end_cycle(cycle));
+            if (h->opt.mode == 1) cs.converged = true;
             return PD_OK;
         }
-        if (cycle < max_cycles) ++cs.restarts;
+        pending = true;
+        PD_TRY(begin_cycle());                    // step 0 of the next cycle from the restart vector
     }
     return PD_OK;
 }
@@ -596,22 +611,20 @@ int rayleigh64(pairdiag *h, int dtype, double *lambda, double *rel)
     const int64_t dim = h->dim;
     PD_TRY(ensure_fp64_pair(h));
     PD_CUDA(convert_launch(0, h->d_v64, dtype, qvec(h, dtype, 0), dim, h->st));
-    PD_TRY(hx(h, 0, h->d_v64, h->d_w64));
     LanczosScalars *S = h->d_S;
+    // w = H v with v^T w fused into the product; v^T v; lambda = v^T w / v^T v
+    // and ||w - lambda v||^2 on the device; one synchronisation
+    PD_TRY(hx(h, 0, h->d_v64, h->d_w64, nullptr, &S->dots[0]));
     unsigned long long *tk = &h->d_tk->vec_done;
-    PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_w64, dim, h->d_part, &S->dots[0], h->st, nullptr, tk));
     PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &S->dots[1], h->st, nullptr, tk));
-    double vv_vw[2];
-    PD_CUDA(cudaMemcpyAsync(vv_vw, &S->dots[0], 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    PD_CUDA(cudaStreamSynchronize(h->st));
-    const double lam = vv_vw[0] / vv_vw[1];
-    PD_CUDA(cudaMemcpyAsync(&S->dots[2], &lam, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    PD_CUDA(quotient_launch(&S->dots[0], &S->dots[1], &S->dots[2], h->st));
     PD_CUDA(residual_launch(h->d_w64, h->d_v64, &S->dots[2], nullptr, dim, h->d_part, &S->dots[3], h->st, tk));
-    double r2;
-    PD_CUDA(cudaMemcpyAsync(&r2, &S->dots[3], sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    double d[4];
+    PD_CUDA(cudaMemcpyAsync(d, S->dots, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     PD_CUDA(cudaStreamSynchronize(h->st));
+    const double lam = d[2], r2 = d[3];
     *lambda = lam;
-    *rel = (r2 == 0.0) ? 0.0 : std::sqrt(r2 / vv_vw[1]) / std::fabs(lam);
+    *rel = (r2 == 0.0) ? 0.0 : std::sqrt(r2 / d[1]) / std::fabs(lam);
     return PD_OK;
 }
 

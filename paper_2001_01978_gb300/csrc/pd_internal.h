@@ -403,6 +403,8 @@ cudaError_t step_launch(int dtype, const StepPlan &plan, const void *Q, int64_t 
                         void *p, int64_t n, double *partials, GridBar *gb, void *qnext, cudaStream_t st);
 // start of a cycle: used = 0, broken = 0, tnorm = 0
 cudaError_t cycle_reset_launch(LanczosScalars *S, cudaStream_t st);
+// *out = *num / *den (one thread)
+cudaError_t quotient_launch(const double *num, const double *den, double *out, cudaStream_t st);
 // after step i of a cycle: when the residual of the lowest Ritz pair of the
 // steps so far is within tol of its Ritz value, set broken (the cycle ends)
 cudaError_t ritz_estimate_launch(LanczosScalars *S, int i, double tol, cudaStream_t st);

@@ -642,6 +642,11 @@ step_kernel(const T *__restrict__ Q, int64_t ldq, int i, LanczosScalars *S, T *p
     }
 }
 
+__global__ void quotient_kernel(const double *num, const double *den, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = *num / *den;
+}
+
 __global__ void cycle_reset_kernel(LanczosScalars *S)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1779,6 +1784,13 @@ cudaError_t recur_project_launch(int dtype, const void *Q, int64_t ld, int i, co
 {
     if (dtype == 0) recur_t<double>((const double *)Q, ld, i, S, (double *)p, n, partials, out, ticket, skip, st);
     else recur_t<float>((const float *)Q, ld, i, S, (float *)p, n, partials, out, ticket, skip, st);
+    return cudaGetLastError();
+}
+
+cudaError_t quotient_launch(const double *num, const double *den, double *out, cudaStream_t st)
+{
+    quotient_kernel<<<1, 32, 0, st>>>(num, den, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
