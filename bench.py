@@ -327,6 +327,9 @@ def run_ours(args):
     clk = clocks.stop()
     hx_count, hx_ms = pd.pairdiag_get_profile(mixed.h)
     hx64_count, hx64_ms = pd.pairdiag_get_profile(mixed.h, pd.PD_PREC_FP64)   # the FP64 refinement products
+    # the vector work of the Lanczos steps that follow the products
+    st32_count, st32_ms = pd.pairdiag_get_profile(mixed.h, pd.PD_PROF_STEP + pd.PD_PREC_MIXED)
+    st64_count, st64_ms = pd.pairdiag_get_profile(mixed.h, pd.PD_PROF_STEP + pd.PD_PREC_FP64)
     pd.pairdiag_set_profiling(mixed.h, False)
 
     total_ms = sum(step_ms)
@@ -418,7 +421,11 @@ def run_ours(args):
                 "hx_nnz_per_s": nnz / avg_hx_s, "hx_share_of_step": (hx_ms + hx64_ms) / total_ms,
                 "hx32_share_of_step": hx_ms / total_ms,
                 "hx_share_is": "all H*x products of a solve (FP32 cycles + FP64 refinement) / solve time",
-                "timed_launches": hx_count, "executed_products": hx_executed}
+                "timed_launches": hx_count, "executed_products": hx_executed,
+                "step_share_of_step": (st32_ms + st64_ms) / total_ms,
+                "step_avg_ms": (st32_ms + st64_ms) / max(1, st32_count + st64_count),
+                "step_share_is": "vector work of the Lanczos steps after each product (recurrence, "
+                                 "full Gram-Schmidt pass, norm, next basis vector) / solve time"}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -468,11 +468,16 @@ int64_t pairdiag_kernel_launches(void);
 
 /*
  * Kernel timing of the handle's H*x launches: while enabled (on != 0), every
- * H*x launch of the handle is bracketed by CUDA events on the handle's stream.
+ * H*x launch of the handle is bracketed by CUDA events on the handle's stream,
+ * and so is the vector work of every Lanczos step that follows a product (the
+ * fused step launch, or the recurrence/projection and update launches, with
+ * the projection against locked states where there are any).
  * pairdiag_get_profile synchronises the stream, returns the number of timed
- * launches of the given precision (PD_PREC_FP64 or PD_PREC_MIXED = FP32; a
- * negative precision: all of them) and their summed duration in milliseconds,
- * and clears the records it returned (those of the other precision stay).
+ * regions of the given kind and their summed duration in milliseconds, and
+ * clears the records it returned (those of other kinds stay).  Kinds:
+ * PD_PREC_FP64 or PD_PREC_MIXED (= FP32) H*x launches, a negative value for
+ * both; 2 + PD_PREC_FP64 or 2 + PD_PREC_MIXED for the steps on FP64 or FP32
+ * vectors.
  */
 int pairdiag_set_profiling(pairdiag_t *h, int on);
 int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, double *hx_ms);

@@ -328,23 +328,32 @@ int ensure_fp64_pair(pairdiag *h)
     return PD_OK;
 }
 
+// While profiling: a pair of events for one timed region of record kind
+// `code` (0/1: an H*x launch of that precision; 2 + dtype: the vector work of
+// one Lanczos step), its start recorded on the handle's stream; else nullptr
+int prof_begin(pairdiag *h, int code, std::pair<cudaEvent_t, cudaEvent_t> **ev)
+{
+    *ev = nullptr;
+    if (!h->profiling) return PD_OK;
+    if (h->hx_events_used == h->hx_events.size()) {
+        std::pair<cudaEvent_t, cudaEvent_t> e2;
+        PD_CUDA(cudaEventCreate(&e2.first));
+        PD_CUDA(cudaEventCreate(&e2.second));
+        h->hx_events.push_back(e2);
+        h->hx_event_prec.push_back(0);
+    }
+    h->hx_event_prec[h->hx_events_used] = code;
+    *ev = &h->hx_events[h->hx_events_used++];
+    PD_CUDA(cudaEventRecord((*ev)->first, h->st));
+    return PD_OK;
+}
+
 // y = H x; with dot_out also x^T y -> *dot_out (fused into the same launch)
 int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nullptr, double *dot_out = nullptr)
 {
     HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
     std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
-    if (h->profiling) {
-        if (h->hx_events_used == h->hx_events.size()) {
-            std::pair<cudaEvent_t, cudaEvent_t> e2;
-            PD_CUDA(cudaEventCreate(&e2.first));
-            PD_CUDA(cudaEventCreate(&e2.second));
-            h->hx_events.push_back(e2);
-            h->hx_event_prec.push_back(0);
-        }
-        h->hx_event_prec[h->hx_events_used] = precision;
-        ev = &h->hx_events[h->hx_events_used++];
-        PD_CUDA(cudaEventRecord(ev->first, h->st));
-    }
+    PD_TRY(prof_begin(h, precision, &ev));
     const HxDot dot{h->d_blkdot, dot_out};
     PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_tk, h->hxgrid[precision], h->st, skip,
                       dot_out ? &dot : nullptr));
@@ -436,14 +445,17 @@ int lanczos_step(pairdiag *h, int dtype, int i, int m)
     const int64_t ld = h->ldq;
     unsigned long long *tk = &h->d_tk->vec_done;
     PD_TRY(hx(h, dtype, qvec(h, dtype, i), p, skip, S->c1));
+    std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
+    PD_TRY(prof_begin(h, 2 + dtype, &ev));
     if (h->n_locked) PD_TRY(lock_project(h, dtype, p, skip));
     if (fused_step(h, dtype)) {
         PD_CUDA(step_launch(dtype, h->step[dtype], Q, ld, i, S, p, dim, h->d_part, &h->d_tk->bar,
                             i + 1 < m ? qvec(h, dtype, i + 1) : nullptr, st));
-        return PD_OK;
+    } else {
+        PD_CUDA(recur_project_launch(dtype, Q, ld, i, S, p, dim, h->d_part, S->c2, st, skip, tk));
+        PD_CUDA(update_launch(dtype, Q, ld, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip, tk, S, i));
     }
-    PD_CUDA(recur_project_launch(dtype, Q, ld, i, S, p, dim, h->d_part, S->c2, st, skip, tk));
-    PD_CUDA(update_launch(dtype, Q, ld, i + 1, S->c2, p, dim, h->d_part, &S->norm2, st, skip, tk, S, i));
+    if (ev) PD_CUDA(cudaEventRecord(ev->second, st));
     return PD_OK;
 }
 
@@ -860,7 +872,8 @@ int pairdiag_get_profile(pairdiag_t *h, int precision, int64_t *hx_launches, dou
     int64_t count = 0;
     size_t kept = 0;                              // records of other precisions stay, in order
     for (size_t i = 0; i < h->hx_events_used; ++i) {
-        if (precision >= 0 && h->hx_event_prec[i] != precision) {
+        const int code = h->hx_event_prec[i];
+        if (precision >= 0 ? code != precision : code >= 2) {
             std::swap(h->hx_events[kept], h->hx_events[i]);
             std::swap(h->hx_event_prec[kept], h->hx_event_prec[i]);
             ++kept;

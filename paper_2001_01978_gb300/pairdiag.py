@@ -466,9 +466,13 @@ def pairdiag_set_step_fusion(h, on: bool) -> None:
     _check(lib().pairdiag_set_step_fusion(h, 1 if on else 0))
 
 
+PD_PROF_STEP = 2     # record kinds PD_PROF_STEP + PD_PREC_*: the Lanczos steps' vector work
+
+
 def pairdiag_get_profile(h, precision: int = PD_PREC_MIXED):
-    """(number of timed H*x launches of this precision, their summed duration in
-    ms); clears the records returned (precision < 0: all precisions)."""
+    """(number of timed regions of this kind, their summed duration in ms);
+    clears the records returned.  Kinds: PD_PREC_FP64 / PD_PREC_MIXED H*x
+    launches (negative: both), PD_PROF_STEP + PD_PREC_* the steps' vector work."""
     n = ctypes.c_int64()
     ms = ctypes.c_double()
     _check(lib().pairdiag_get_profile(h, precision, ctypes.byref(n), ctypes.byref(ms)))

@@ -260,3 +260,24 @@ def test_device_cache_reuse_and_release():
         r4 = s.ground_state(1e-5, out=out)
     assert r4["vec"] is out and r4["e0"] == r1["e0"]
     assert np.all(np.isfinite(out)) and abs(np.linalg.norm(out) - 1.0) < 1e-10
+
+
+def test_profile_records_products_and_steps():
+    """Timing records of a mixed solve: every FP32 product is followed by the
+    vector work of its Lanczos step, so the two kinds have equal counts; the
+    FP64 refinement adds FP64 products; each kind is cleared once returned."""
+    omega, n = 16, 8
+    e, G = pd_inputs.separable_noise(omega, seed=7)
+    with pd.Solver(omega, n, e, G, precision=pd.PD_PREC_MIXED) as s:
+        pd.pairdiag_set_profiling(s.h, True)
+        r = s.ground_state(1e-9)
+        assert r["status"] == pd.PD_OK
+        n32, ms32 = pd.pairdiag_get_profile(s.h, pd.PD_PREC_MIXED)
+        n64, ms64 = pd.pairdiag_get_profile(s.h, pd.PD_PREC_FP64)
+        s32, sms32 = pd.pairdiag_get_profile(s.h, pd.PD_PROF_STEP + pd.PD_PREC_MIXED)
+        s64, sms64 = pd.pairdiag_get_profile(s.h, pd.PD_PROF_STEP + pd.PD_PREC_FP64)
+        pd.pairdiag_set_profiling(s.h, False)
+        assert n32 > 0 and s32 == n32 and ms32 > 0 and sms32 > 0
+        assert n64 >= 1 and s64 <= n64
+        assert pd.pairdiag_get_profile(s.h, -1) == (0, 0.0)
+        assert pd.pairdiag_get_profile(s.h, pd.PD_PROF_STEP + pd.PD_PREC_MIXED) == (0, 0.0)
