@@ -41,6 +41,13 @@ struct TuneKey {
 std::mutex g_tune_mutex;
 std::map<TuneKey, std::pair<int, int>> g_tune;
 
+// Largest-first block order for the full-space H*x: built for at most
+// kLptMaxBlocks blocks, used while a launch has at most kLptPerCta blocks per
+// CTA (beyond that the tail of one block is a small part of a launch, and the
+// ascending order keeps concurrently processed blocks close in the basis)
+constexpr int64_t kLptMaxBlocks = (int64_t)1 << 18;
+constexpr int64_t kLptPerCta = 64;
+
 bool tuned_schedule(int omega, int n, int precision, int *low_bits, int *variant)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -137,6 +144,10 @@ struct pairdiag {
     int64_t full_dim = 0, full_nnz = 0;   // C(Omega, N) and its off-diagonal nonzeros
     int32_t *d_kmap = nullptr;       // truncated space (Sec. 3.5): full index -> kept index, -1 dropped
     uint64_t *d_kblk_h = nullptr, *d_kblk_base = nullptr;   // the blocks holding kept states
+    // the block list in the order the persistent H*x kernels take it when
+    // there are few blocks per CTA: largest blocks first (ascending high word
+    // within a size), so the launch does not end on one CTA's large block
+    uint64_t *d_lpt_h = nullptr, *d_lpt_base = nullptr;
     Blocks B{};
     int device = 0;
     cudaStream_t st = nullptr;
@@ -194,7 +205,8 @@ void free_all(pairdiag *h)
     void *ptrs[] = {h->d_blk_h, h->d_blk_base, h->d_binom, h->d_lowword, h->d_rankL, h->d_G64,
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64,
-                    h->d_L64, h->d_L32, h->d_lockc, h->d_kmap, h->d_kblk_h, h->d_kblk_base};
+                    h->d_L64, h->d_L32, h->d_lockc, h->d_kmap, h->d_kblk_h, h->d_kblk_base,
+                    h->d_lpt_h, h->d_lpt_base};
     // the blocks go back to the library's cache: no queued kernel may still use
     // them.  Every kernel and copy of the handle runs on its stream, so that
     // stream's completion is enough (other streams of the caller go on).
@@ -279,6 +291,19 @@ int build_tables(pairdiag *h)
 
     PD_TRY(upload(&h->d_blk_h, hw));
     PD_TRY(upload(&h->d_blk_base, base));
+    if ((int64_t)hw.size() <= kLptMaxBlocks) {
+        std::vector<uint32_t> order(hw.size());
+        for (size_t b = 0; b < order.size(); ++b) order[b] = (uint32_t)b;
+        auto rows = [&](uint32_t b) { return host_binom(L, N - __builtin_popcountll(hw[b])); };
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return rows(a) > rows(b); });
+        std::vector<uint64_t> lh(hw.size()), lb(hw.size());
+        for (size_t b = 0; b < order.size(); ++b) {
+            lh[b] = hw[order[b]];
+            lb[b] = base[order[b]];
+        }
+        PD_TRY(upload(&h->d_lpt_h, lh));
+        PD_TRY(upload(&h->d_lpt_base, lb));
+    }
     PD_TRY(upload(&h->d_lowword, lowword));
     PD_TRY(upload(&h->d_rankL, rankL));
     PD_TRY(upload(&h->d_binom, binom));
@@ -355,7 +380,12 @@ int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nul
     std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
     PD_TRY(prof_begin(h, precision, &ev));
     const HxDot dot{h->d_blkdot, dot_out};
-    PD_CUDA(hx_launch(h->B, P, precision, x, y, h->d_tk, h->hxgrid[precision], h->st, skip,
+    Blocks B = h->B;
+    if (h->d_lpt_h && !B.kept_map && B.nblocks <= kLptPerCta * (int64_t)h->hxgrid[precision]) {
+        B.blk_h = h->d_lpt_h;
+        B.blk_base = h->d_lpt_base;
+    }
+    PD_CUDA(hx_launch(B, P, precision, x, y, h->d_tk, h->hxgrid[precision], h->st, skip,
                       dot_out ? &dot : nullptr));
     if (ev) PD_CUDA(cudaEventRecord(ev->second, h->st));
     return PD_OK;
