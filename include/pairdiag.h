@@ -55,6 +55,7 @@ extern "C" {
 #define PD_PREC_FP64  0  /* FP64 vectors, FP64 row accumulation */
 #define PD_PREC_MIXED 1  /* FP32 vectors + FP32 row sums; FP64 dots, FP64 tridiagonal
                             solve and a final FP64 Rayleigh-quotient refinement */
+#define PD_HX_FLOATFLOAT 2  /* pairdiag_hx_dev only: float x, double y, float-float rows */
 
 /* start vector of the first Lanczos cycle */
 #define PD_START_RANDOM 0  /* counter-based SplitMix64 uniform in [-1,1), seeded */
@@ -164,6 +165,13 @@ int pairdiag_rank_dev(const pairdiag_t *h, const uint64_t *states_dev, int64_t c
  * elements in basis order.
  *   precision PD_PREC_FP64: x_dev, y_dev are double; FP64 row sums.
  *   precision PD_PREC_MIXED: x_dev, y_dev are float; FP32 row sums, G rounded to FP32.
+ *   precision PD_HX_FLOATFLOAT: x_dev is float, y_dev is double; every
+ *     coefficient is split into two FP32 parts, each product with an element
+ *     of x is exact in its high part, and the row sums are float-float, so the
+ *     rows are as accurate as FP64 sums of the FP32 x while the arithmetic
+ *     runs on the FP32 pipes.  The mixed form's FP64 Rayleigh refinement takes
+ *     this product.  PD_ENOTSUP on a truncated handle or where its shared
+ *     memory does not fit.
  * x_dev and y_dev must not overlap.  Asynchronous.
  */
 int pairdiag_hx_dev(pairdiag_t *h, int precision, const void *x_dev, void *y_dev);

@@ -156,13 +156,14 @@ struct pairdiag {
     uint16_t *d_lowword = nullptr, *d_rankL = nullptr;
     double *d_G64 = nullptr, *d_d64 = nullptr;
     float *d_G32 = nullptr, *d_d32 = nullptr;
+    float2 *d_Gff = nullptr, *d_dff = nullptr;   // G and d split into two FP32 parts (float-float rows)
     Tickets *d_tk = nullptr;         // counters of the persistent and streaming kernels
     double *d_blkdot = nullptr;      // [nblocks] per-block partial sums of the fused alpha
     double *d_part = nullptr;        // partial sums of the streaming kernels
     size_t part_count = 0;
     LanczosScalars *d_S = nullptr;
     double *d_small = nullptr;       // [8] small outputs
-    int hxgrid[2] = {0, 0};
+    int hxgrid[3] = {0, 0, 0};       // per H*x precision (2: float-float rows; 0 = not available)
     int rgrid = 0;                   // grid of the per-row reductions
     // Lanczos window (lazily allocated) per storage type
     void *d_Q[2] = {nullptr, nullptr};
@@ -206,7 +207,7 @@ void free_all(pairdiag *h)
                     h->d_d64, h->d_G32, h->d_d32, h->d_tk, h->d_blkdot, h->d_part, h->d_S, h->d_small,
                     h->d_Q[0], h->d_Q[1], h->d_p[0], h->d_p[1], h->d_v64, h->d_w64,
                     h->d_L64, h->d_L32, h->d_lockc, h->d_kmap, h->d_kblk_h, h->d_kblk_base,
-                    h->d_lpt_h, h->d_lpt_base};
+                    h->d_lpt_h, h->d_lpt_base, h->d_Gff, h->d_dff};
     // the blocks go back to the library's cache: no queued kernel may still use
     // them.  Every kernel and copy of the handle runs on its stream, so that
     // stream's completion is enough (other streams of the caller go on).
@@ -376,9 +377,9 @@ int prof_begin(pairdiag *h, int code, std::pair<cudaEvent_t, cudaEvent_t> **ev)
 // y = H x; with dot_out also x^T y -> *dot_out (fused into the same launch)
 int hx(pairdiag *h, int precision, const void *x, void *y, const int *skip = nullptr, double *dot_out = nullptr)
 {
-    HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32};
+    HxProblem P{h->d_G64, h->d_d64, h->d_G32, h->d_d32, h->d_Gff, h->d_dff};
     std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
-    PD_TRY(prof_begin(h, precision, &ev));
+    PD_TRY(prof_begin(h, precision == 2 ? 0 : precision, &ev));    // float-float rows count as FP64
     const HxDot dot{h->d_blkdot, dot_out};
     Blocks B = h->B;
     if (h->d_lpt_h && !B.kept_map && B.nblocks <= kLptPerCta * (int64_t)h->hxgrid[precision]) {
@@ -655,8 +656,11 @@ int rayleigh64(pairdiag *h, int dtype, double *lambda, double *rel)
     PD_CUDA(convert_launch(0, h->d_v64, dtype, qvec(h, dtype, 0), dim, h->st));
     LanczosScalars *S = h->d_S;
     // w = H v with v^T w fused into the product; v^T v; lambda = v^T w / v^T v
-    // and ||w - lambda v||^2 on the device; one synchronisation
-    PD_TRY(hx(h, 0, h->d_v64, h->d_w64, nullptr, &S->dots[0]));
+    // and ||w - lambda v||^2 on the device; one synchronisation.  An FP32 v
+    // (the mixed form) takes the float-float product: rows as accurate as FP64
+    // sums, on the FP32 pipes
+    if (dtype == 1 && h->hxgrid[2] > 0) PD_TRY(hx(h, 2, qvec(h, dtype, 0), h->d_w64, nullptr, &S->dots[0]));
+    else PD_TRY(hx(h, 0, h->d_v64, h->d_w64, nullptr, &S->dots[0]));
     unsigned long long *tk = &h->d_tk->vec_done;
     PD_CUDA(multidot_launch(0, h->d_v64, dim, 1, h->d_v64, dim, h->d_part, &S->dots[1], h->st, nullptr, tk));
     PD_CUDA(quotient_launch(&S->dots[0], &S->dots[1], &S->dots[2], h->st));
@@ -844,16 +848,27 @@ int pairdiag_create(int omega, int n_pairs, const double *e, const double *G,
         if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); st = fail(PD_ECUDA, "no CUDA device"); break; }
         if ((st = build_tables(h)) != PD_OK) break;
         std::vector<float> G32(h->G.begin(), h->G.end()), d32(h->d.begin(), h->d.end());
+        auto split = [](const std::vector<double> &v) {
+            std::vector<float2> r(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float hi = (float)v[i];
+                r[i] = make_float2(hi, (float)(v[i] - (double)hi));
+            }
+            return r;
+        };
         if ((st = upload(&h->d_G64, h->G)) != PD_OK) break;
         if ((st = upload(&h->d_d64, h->d)) != PD_OK) break;
         if ((st = upload(&h->d_G32, G32)) != PD_OK) break;
         if ((st = upload(&h->d_d32, d32)) != PD_OK) break;
+        if ((st = upload(&h->d_Gff, split(h->G))) != PD_OK) break;
+        if ((st = upload(&h->d_dff, split(h->d))) != PD_OK) break;
         if ((st = dalloc(&h->d_tk, 1)) != PD_OK) break;
         if (cudaMemset(h->d_tk, 0, sizeof(Tickets)) != cudaSuccess) { st = fail(PD_ECUDA, "memset"); break; }
         if ((st = dalloc(&h->d_blkdot, (size_t)h->B.nblocks)) != PD_OK) break;
         h->ldq = (h->dim + 3) / 4 * 4;
         h->hxgrid[0] = hx_grid(h->B, 0);
         h->hxgrid[1] = hx_grid(h->B, 1);
+        h->hxgrid[2] = hx_grid(h->B, 2);
         h->rgrid = (int)std::min<int64_t>(h->B.nblocks, vec_grid());
         h->part_count = (size_t)std::max(vec_grid(), h->rgrid) * kMaxWindow;
         if ((st = dalloc(&h->d_part, h->part_count)) != PD_OK) break;
@@ -965,8 +980,11 @@ int pairdiag_rank_dev(const pairdiag_t *h, const uint64_t *states_dev, int64_t c
 int pairdiag_hx_dev(pairdiag_t *h, int precision, const void *x_dev, void *y_dev)
 {
     if (!h || !x_dev || !y_dev) return fail(PD_EINVAL, "null argument");
-    if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED) return fail(PD_EINVAL, "bad precision");
+    if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_HX_FLOATFLOAT)
+        return fail(PD_EINVAL, "bad precision");
     if (x_dev == y_dev) return fail(PD_EINVAL, "x and y must not overlap");
+    if (precision == PD_HX_FLOATFLOAT && h->hxgrid[2] < 1)
+        return fail(PD_ENOTSUP, "no float-float product for this handle (truncated space or shared memory)");
     return hx(h, precision, x_dev, y_dev);
 }
 
@@ -1146,6 +1164,7 @@ void drop_space(pairdiag *h)
     h->ldq = (h->dim + 3) / 4 * 4;
     h->hxgrid[0] = hx_grid(h->B, 0);
     h->hxgrid[1] = hx_grid(h->B, 1);
+        h->hxgrid[2] = hx_grid(h->B, 2);
 }
 
 // The kept states of Sec. 3.5 and the map full index -> kept index.  Returns
@@ -1269,6 +1288,7 @@ int pairdiag_truncate(pairdiag_t *h, int64_t dimension_limit, int64_t bins, int6
         h->B.kept_blk_base = h->d_kblk_base;
         h->hxgrid[0] = hx_grid(h->B, 0);
         h->hxgrid[1] = hx_grid(h->B, 1);
+        h->hxgrid[2] = hx_grid(h->B, 2);
         // off-diagonal nonzeros of the truncated matrix: H x with every G_ij = 1
         // and d = 0 on x = 1 counts each row's kept targets (exact in FP64)
         rc = [&]() -> int {

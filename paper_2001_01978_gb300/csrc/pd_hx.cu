@@ -22,6 +22,7 @@
 #include "pd_internal.h"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace pd {
 namespace {
@@ -88,17 +89,55 @@ __device__ __forceinline__ T x_kept(const T *__restrict__ x, const int32_t *__re
     return m >= 0 ? __ldg(x + m) : T(0);
 }
 
+// Float-float number hi + lo: the row sums of the FP64-accurate product of an
+// FP32 vector, on the FP32 pipes (GB300 issues FP32 FMAs at 64 times its FP64
+// rate).  A coefficient c is stored split, hi = fl(c), lo = fl(c - hi); its
+// product with a vector element x, an FP32 value, is hi*x exactly (the
+// rounding error recovered with one FMA) plus lo*x rounded once, so a product
+// carries a relative error near 2^-48.  Sums add the high parts with Knuth's
+// TwoSum and collect the low parts and the TwoSum errors in lo.
+struct FF {
+    float hi, lo;
+    FF() = default;
+    __host__ __device__ FF(float x) : hi(x), lo(0.0f) {}
+    __host__ __device__ FF(float h, float l) : hi(h), lo(l) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator float() const { return hi + lo; }
+};
+// a coefficient times a vector element (the element's lo is 0)
+__device__ __forceinline__ FF operator*(FF c, FF x)
+{
+    const float p = c.hi * x.hi;
+    return FF(p, fmaf(c.lo, x.hi, fmaf(c.hi, x.hi, -p)));
+}
+__device__ __forceinline__ FF &operator+=(FF &a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float z = s - a.hi;
+    const float t = (a.hi - (s - z)) + (b.hi - z);
+    a.lo += b.lo + t;
+    a.hi = s;
+    return a;
+}
+__device__ __forceinline__ FF operator+(FF a, FF b)
+{
+    a += b;
+    return a;
+}
+
 // x^T y over this warp's rows of one basis block (y as stored) into sw[warp]
 // (lane 0).  No barrier: thread 0 adds the warp sums in warp order after the
 // barrier that opens the next block (block_sum_deferred).
 template <typename T, typename A, int R>
 __device__ __forceinline__ void warp_dot(const A *acc, const T *sx, int nk, double *sw)
 {
-    DotAcc<T> d;
+    // float-float rows: the dot in FP64 of the rows as written (FP64)
+    using D = typename std::conditional<std::is_same<A, FF>::value, double, T>::type;
+    DotAcc<D> d;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int r = threadIdx.x + i * kThreads;
-        if (r < nk) d.add(sx[r], T(acc[i]));
+        if (r < nk) d.add((D)sx[r], D(acc[i]));
     }
     const double s = warp_reduce(d);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
@@ -821,11 +860,11 @@ struct Smem3 {
 // takes row r, and warp w the hops of class index w, w + 8, ...; warp 0 adds
 // the eight partial sums in warp order (a fixed order).  acc[0] of warp 0
 // holds the row's diagonal and low->low terms on entry and the row's y on
-// exit; y is written here.
-template <typename T, typename A, int R>
+// exit; y (of type TY) is written here.
+template <typename T, typename A, int R, typename TY>
 __device__ __forceinline__ void hx3_small(const Smem3<T, A> &s, const int L, const int k, const int ph,
                                           const int nemp, const int nhh, const uint64_t base,
-                                          const uint16_t *__restrict__ lw, T *__restrict__ y, const int nk,
+                                          const uint16_t *__restrict__ lw, TY *__restrict__ y, const int nk,
                                           A (&acc)[R])
 {
     constexpr int kW = kThreads / 32;
@@ -868,16 +907,16 @@ __device__ __forceinline__ void hx3_small(const Smem3<T, A> &s, const int L, con
 #pragma unroll
         for (int q = 0; q < kW; ++q) t += s.part[q * 32 + r];
         acc[0] = t;
-        y[base + r] = T(t);
+        y[base + r] = TY(t);
     }
 }
 
 // The rows of one block in variant 3 (RR rows per thread): diagonal, low->low
 // from the staged block, then the gathers; writes y and the fused dot.
-template <typename T, typename A, int RR, bool DEEP>
+template <typename T, typename A, int RR, bool DEEP, typename TY>
 __device__ __forceinline__ void hx3_rows(const Smem3<T, A> &s, const int omega, const int L, const uint64_t h,
                                          const uint64_t base, const uint16_t *__restrict__ lw,
-                                         T *__restrict__ y, double *swdot, const int k, const int ph,
+                                         TY *__restrict__ y, double *swdot, const int k, const int ph,
                                          const int nemp, const int nhh, const int nk)
 {
     const int tid = threadIdx.x;
@@ -1017,18 +1056,18 @@ __device__ __forceinline__ void hx3_rows(const Smem3<T, A> &s, const int omega, 
 #pragma unroll
     for (int i = 0; i < RR; ++i) {
         const int r = tid + i * kThreads;
-        if (r < nk) y[base + r] = T(acc[i]);
+        if (r < nk) y[base + r] = TY(acc[i]);
     }
     if (swdot) warp_dot<T, A, RR>(acc, s.x, nk, swdot);
 }
 
 // One basis block of y = H x in variant 3.  Called by every thread after a
 // barrier that frees the previous block's shared memory.
-template <typename T, typename A, int R, bool DEEP>
+template <typename T, typename A, int R, bool DEEP, typename TY>
 __device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega, const int L, const int H,
                                           const int N, const uint64_t h, const uint64_t base,
                                           const uint16_t *__restrict__ lowword, const T *__restrict__ x,
-                                          T *__restrict__ y, double *swdot)
+                                          TY *__restrict__ y, double *swdot)
 {
     const int tid = threadIdx.x;
     const int ph = __popcll(h);
@@ -1125,11 +1164,12 @@ __device__ __forceinline__ void hx3_block(const Smem3<T, A> &s, const int omega,
 }
 
 // OCC: resident CTAs per SM the register budget is cut for (4: 64 registers;
-// 5: 48 registers, variant 5, more warps to hide the gathers' latency)
-template <typename T, typename A, int R, bool DEEP, int OCC = 4>
+// 5: 48 registers, variant 5, more warps to hide the gathers' latency).
+// TY: the type of y (double for float-float rows of an FP32 x)
+template <typename T, typename A, int R, bool DEEP, int OCC = 4, typename TY = T>
 __global__ void __launch_bounds__(kThreads, OCC)
 hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, const T *__restrict__ x,
-           T *__restrict__ y, Tickets *tk, const int *__restrict__ skip, double *blk_part, double *dot_out)
+           TY *__restrict__ y, Tickets *tk, const int *__restrict__ skip, double *blk_part, double *dot_out)
 {
     if (skip && *skip) return;                    // CTA-uniform
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1512,6 +1552,62 @@ __global__ void occ_final(const double *__restrict__ part, int n, int omega, dou
     out[p] = 2.0 * s;
 }
 
+// ---- float-float rows of an FP32 vector (FP64-accurate, y in FP64) -----------
+// Variant 3's kernel with FF coefficients and row sums: x float, y double.
+bool ff_fits(const Blocks &B)
+{
+    return !B.kept_map && layout3<float, FF>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total <= kSmemLimit;
+}
+
+template <int R>
+const void *ff_fn()
+{
+    return (const void *)hx3_kernel<float, FF, R, false, 4, double>;
+}
+
+const void *ff_fn_rows(int rows)
+{
+    return rows <= 1 ? ff_fn<1>() : rows <= 2 ? ff_fn<2>() : rows <= 4 ? ff_fn<4>() : ff_fn<8>();
+}
+
+int grid_ff(const Blocks &B)
+{
+    const size_t smem = layout3<float, FF>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total;
+    const void *fn = ff_fn_rows((B.max_block + kThreads - 1) / kThreads);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > B.nblocks) g = B.nblocks;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <int R>
+cudaError_t launch_ff_r(const Blocks &B, const FF *G, const FF *d, const float *x, double *y, Tickets *tk,
+                        int grid, cudaStream_t st, const int *skip, const HxDot *dot)
+{
+    const size_t smem = layout3<float, FF>(B.omega, B.L, B.H, B.n, B.max_block, B.max_hh).total;
+    cudaError_t err = cudaFuncSetAttribute(ff_fn<R>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    hx3_kernel<float, FF, R, false, 4, double><<<grid, kThreads, smem, st>>>(
+        B, G, d, x, y, tk, skip, dot ? dot->blk_part : nullptr, dot ? dot->out : nullptr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff(const Blocks &B, const FF *G, const FF *d, const float *x, double *y, Tickets *tk, int grid,
+                      cudaStream_t st, const int *skip, const HxDot *dot)
+{
+    const int rows = (B.max_block + kThreads - 1) / kThreads;
+    if (rows <= 1) return launch_ff_r<1>(B, G, d, x, y, tk, grid, st, skip, dot);
+    if (rows <= 2) return launch_ff_r<2>(B, G, d, x, y, tk, grid, st, skip, dot);
+    if (rows <= 4) return launch_ff_r<4>(B, G, d, x, y, tk, grid, st, skip, dot);
+    return launch_ff_r<8>(B, G, d, x, y, tk, grid, st, skip, dot);
+}
+
 }  // namespace
 
 size_t hx_smem_bytes(const Blocks &B, int precision)
@@ -1527,6 +1623,7 @@ int hx_variant(const Blocks &B, int precision)
 
 int hx_grid(const Blocks &B, int precision)
 {
+    if (precision == 2) return ff_fits(B) ? grid_ff(B) : 0;
     return precision == 0 ? grid_prec<double, double>(B) : grid_prec<float, float>(B);
 }
 
@@ -1534,6 +1631,11 @@ cudaError_t hx_launch(const Blocks &B, const HxProblem &P, int precision, const 
                       Tickets *tk, int grid, cudaStream_t st, const int *skip, const HxDot *dot)
 {
     if (dot && (!dot->blk_part || !dot->out)) return cudaErrorInvalidValue;
+    if (precision == 2) {
+        if (!ff_fits(B) || !P.Gff || !P.dff || grid < 1) return cudaErrorNotSupported;
+        return launch_ff(B, reinterpret_cast<const FF *>(P.Gff), reinterpret_cast<const FF *>(P.dff),
+                         static_cast<const float *>(x), static_cast<double *>(y), tk, grid, st, skip, dot);
+    }
     if (precision == 0) return launch_prec<double, double>(B, P.G64, P.d64, x, y, tk, grid, st, skip, dot);
     return launch_prec<float, float>(B, P.G32, P.d32, x, y, tk, grid, st, skip, dot);
 }

@@ -288,9 +288,13 @@ __device__ __forceinline__ double reduce_partials(const double *part, int nb, in
 // ---- H*x (pd_hx.cu) -------------------------------------------------------
 // precision 0: double vectors / double accumulation with G64, d64
 // precision 1: float vectors / float accumulation with G32, d32
+// precision 2: float x (taken as exact), double y; float-float products and row
+//              sums with Gff, dff (each value split as hi = fl(v), lo = fl(v - hi)):
+//              FP64-accurate rows on the FP32 pipes (variant 3, full space only)
 struct HxProblem {
     const double *G64, *d64;         // G [omega*omega], d_p = 2 e_p + G_pp
     const float *G32, *d32;
+    const float2 *Gff, *dff;
 };
 // batched H*x: skip[p * skip_stride] != 0 passes over problem p (skip nullable).
 // counter: two zeroed device counters (next block, finished CTAs); the last CTA

@@ -16,6 +16,7 @@ from . import build as _build
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ENOCONV, PD_ETIMEOUT, PD_ECUDA, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 PD_PREC_FP64, PD_PREC_MIXED = 0, 1
+PD_HX_FLOATFLOAT = 2     # pairdiag_hx_dev only: float x, double y, float-float rows
 PD_START_RANDOM, PD_START_FIRST, PD_START_HF, PD_START_USER, PD_START_MLP = 0, 1, 2, 3, 4
 (PD_MLP_Z1, PD_MLP_A1, PD_MLP_Z2, PD_MLP_A2, PD_MLP_Z3, PD_MLP_A3, PD_MLP_OUT, PD_MLP_DOUT, PD_MLP_DZ3, PD_MLP_DA2,
  PD_MLP_DZ2, PD_MLP_DA1, PD_MLP_DZ1) = range(13)
@@ -244,12 +245,17 @@ def pairdiag_rank_dev(h, states, ranks) -> None:
 
 
 def pairdiag_hx_dev(h, precision: int, x, y) -> None:
+    """y = H x on device tensors: PD_PREC_FP64 (double x, y), PD_PREC_MIXED
+    (float x, y) or PD_HX_FLOATFLOAT (float x, double y)."""
     import torch
-    dt = torch.float64 if precision == PD_PREC_FP64 else torch.float32
+    if precision == PD_HX_FLOATFLOAT:
+        dx, dy = torch.float32, torch.float64
+    else:
+        dx = dy = torch.float64 if precision == PD_PREC_FP64 else torch.float32
     dim = pairdiag_dim(h)
     if x.numel() < dim or y.numel() < dim:
         raise ValueError(f"x and y need dim = {dim} elements")
-    _check(lib().pairdiag_hx_dev(h, precision, _dev_ptr(x, dt), _dev_ptr(y, dt)))
+    _check(lib().pairdiag_hx_dev(h, precision, _dev_ptr(x, dx), _dev_ptr(y, dy)))
 
 
 def pairdiag_hx(h, x) -> np.ndarray:

@@ -166,6 +166,49 @@ def test_hx_fp32_vs_oracle(omega, n, low):
         assert np.all(np.abs(got - ref) <= bound)
 
 
+EPS_FF = 2.0 ** -44     # per term: float-float products and sums (about 2^-48), with margin
+
+
+@pytest.mark.parametrize("omega,n,low", [(12, 6, 0), (16, 5, 0), (20, 10, 0), (22, 4, 0), (24, 12, 0),
+                                         (17, 16, 0), (19, 9, 3), (10, 0, 0), (10, 10, 0), (18, 9, 13)])
+def test_hx_floatfloat_vs_oracle(omega, n, low):
+    """Float-float rows of an FP32 vector (the product the mixed form's FP64
+    Rayleigh refinement takes) against the oracle's FP64 H*x of the same values,
+    element by element, under a bound of 2^-44 per term of a row; FP32 row sums
+    of the same vector miss that bound by orders of magnitude, so the test
+    tells the two apart."""
+    e, G = pd_inputs.separable_noise(omega, seed=omega + 31 * n + 5)
+    with pd.Solver(omega, n, e, G, low_bits=low) as s:
+        x32 = pd_inputs.random_vector(s.dim, omega * 11 + n).astype(np.float32)
+        xt = torch.from_numpy(x32).cuda()
+        yt = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+        pd.pairdiag_hx_dev(s.h, pd.PD_HX_FLOATFLOAT, xt, yt)
+        got = yt.cpu().numpy()
+        y32 = torch.empty_like(xt)
+        pd.pairdiag_hx_dev(s.h, pd.PD_PREC_MIXED, xt, y32)
+        got32 = y32.cpu().numpy().astype(np.float64)
+    x = x32.astype(np.float64)
+    b = oracle.basis(omega, n)
+    ref = oracle.hx(omega, n, e, G, x, b)
+    bound = hx_bound(omega, n, abs_row_scale(omega, n, e, G, x, basis=b), EPS_FF)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / np.maximum(bound, 1e-300))
+    if s.dim > 100:
+        assert np.any(np.abs(got32 - ref) > bound)
+
+
+def test_hx_floatfloat_not_on_truncated_space():
+    """The float-float product covers the full space only: a truncated handle
+    answers PD_ENOTSUP (and its mixed solves refine with the FP64 product)."""
+    e, G = pd_inputs.separable_noise(14, seed=3)
+    with pd.Solver(14, 7, e, G) as s:
+        pd.pairdiag_truncate(s.h, 1000)
+        xt = torch.ones(s.dim, dtype=torch.float32, device="cuda")
+        yt = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+        with pytest.raises(pd.PairDiagError) as ex:
+            pd.pairdiag_hx_dev(s.h, pd.PD_HX_FLOATFLOAT, xt, yt)
+        assert ex.value.code == pd.PD_ENOTSUP
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("omega,n,low", [(16, 5, 0), (20, 10, 0), (19, 9, 3), (15, 7, 8), (22, 4, 0), (24, 12, 13),
                                          (26, 3, 12), (21, 2, 9), (18, 16, 10), (12, 6, 12), (23, 1, 8), (20, 19, 11)])
