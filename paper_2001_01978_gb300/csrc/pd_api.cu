@@ -1164,7 +1164,7 @@ void drop_space(pairdiag *h)
     h->ldq = (h->dim + 3) / 4 * 4;
     h->hxgrid[0] = hx_grid(h->B, 0);
     h->hxgrid[1] = hx_grid(h->B, 1);
-        h->hxgrid[2] = hx_grid(h->B, 2);
+    h->hxgrid[2] = hx_grid(h->B, 2);
 }
 
 // The kept states of Sec. 3.5 and the map full index -> kept index.  Returns
