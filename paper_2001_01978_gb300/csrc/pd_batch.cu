@@ -232,7 +232,7 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
     buf.st = c.st;
     BatchDesc *d_desc; uint32_t *d_bp; uint64_t *d_bh, *d_bb, *d_binom;
     uint16_t *d_lw, *d_rk;
-    double *d_G64, *d_d64; float *d_G32, *d_d32;
+    double *d_G64, *d_d64; float *d_G32, *d_d32; float2 *d_Gff, *d_dff;
     int *d_cp, *d_cl, *d_pc0, *d_pnc; int64_t *d_cs, *d_po;
     std::vector<uint64_t> binom(64 * 64);
     for (int i = 0; i < 64; ++i)
@@ -248,6 +248,18 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
     PD_TRY(buf.upload(&d_d64, d64));
     PD_TRY(buf.upload(&d_G32, G32));
     PD_TRY(buf.upload(&d_d32, d32));
+    {   // G and d split into two FP32 parts: the float-float refinement product
+        auto split = [](const std::vector<double> &v) {
+            std::vector<float2> r(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float hi = (float)v[i];
+                r[i] = make_float2(hi, (float)(v[i] - (double)hi));
+            }
+            return r;
+        };
+        PD_TRY(buf.upload(&d_Gff, split(G64)));
+        PD_TRY(buf.upload(&d_dff, split(d64)));
+    }
     PD_TRY(buf.upload(&d_cp, chunk_prob));
     PD_TRY(buf.upload(&d_cl, chunk_len));
     PD_TRY(buf.upload(&d_cs, chunk_start));
@@ -267,7 +279,7 @@ int setup_class(ClassRun &c, const pairdiag_options &opt, const int *omega, cons
     V.count = count; V.nchunks = (int)chunk_prob.size(); V.total = total;
     V.chunk_prob = d_cp; V.chunk_start = d_cs; V.chunk_len = d_cl;
     V.prob_chunk0 = d_pc0; V.prob_nchunk = d_pnc; V.prob_off = d_po;
-    c.P = HxProblem{d_G64, d_d64, d_G32, d_d32};
+    c.P = HxProblem{d_G64, d_d64, d_G32, d_d32, d_Gff, d_dff};
     c.total = total;
 
     PD_TRY(buf.alloc(&c.part, (size_t)V.nchunks * kMaxWindow));
@@ -434,7 +446,11 @@ int launch_class(ClassRun &c, const pairdiag_options &opt, double tol)
     const int64_t total = c.total;
     const int sd = (int)(sizeof(BatchState) / sizeof(double));
     PD_CUDA(convert_launch(0, c.v64, 1, c.Q32, total, st));
-    PD_CUDA(hx_batch_launch(c.BB, c.P, 0, c.v64, c.w64, c.counter, hx_batch_grid(c.BB, 0), st, nullptr, 0));
+    // w = H v: float-float rows of the FP32 restart vectors where the kernel
+    // fits (FP64-accurate, on the FP32 pipes), else FP64 rows of v64
+    const int ffg = hx_batch_grid(c.BB, 2);
+    if (ffg > 0) PD_CUDA(hx_batch_launch(c.BB, c.P, 2, c.Q32, c.w64, c.counter, ffg, st, nullptr, 0));
+    else PD_CUDA(hx_batch_launch(c.BB, c.P, 0, c.v64, c.w64, c.counter, hx_batch_grid(c.BB, 0), st, nullptr, 0));
     PD_CUDA(seg_dots_launch(0, c.V, c.v64, total, 1, c.w64, nullptr, c.part, &c.S[0].c2[0], sd, st));
     PD_CUDA(seg_dots_launch(0, c.V, c.v64, total, 1, c.v64, nullptr, c.part, &c.S[0].c2[1], sd, st));
     PD_CUDA(batch_rayleigh_launch(c.S, c.count, 0, st));

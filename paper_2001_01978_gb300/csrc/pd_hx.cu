@@ -1209,10 +1209,10 @@ hx3_kernel(const Blocks B, const A *__restrict__ Gg, const A *__restrict__ dg, c
 // rank table and binomials only when the next block it takes belongs to
 // another problem; problems flagged in skip[] are passed over.  The last CTA
 // returns both counters to zero.
-template <typename T, typename A, int R>
+template <typename T, typename A, int R, typename TY = T>
 __global__ void __launch_bounds__(kThreads, 4)
 hx3_batch_kernel(const BatchBlocks BB, const A *__restrict__ Gall, const A *__restrict__ dall,
-                 const T *__restrict__ x, T *__restrict__ y, unsigned long long *counter,
+                 const T *__restrict__ x, TY *__restrict__ y, unsigned long long *counter,
                  const int *__restrict__ skip, int skip_stride)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1714,18 +1714,75 @@ int batch_grid_t(const BatchBlocks &BB)
     if (g > BB.nblocks) g = BB.nblocks;
     return (int)(g > 0 ? g : 1);
 }
+
+// Batched float-float rows of FP32 vectors (x float, y double): the batched
+// variant-3 kernel with FF coefficients, where its shared memory fits
+bool batch_ff_fits(const BatchBlocks &BB)
+{
+    return layout3<float, FF>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh).total <=
+           kSmemLimit;
+}
+
+template <int R>
+const void *batch_ff_fn()
+{
+    return (const void *)hx3_batch_kernel<float, FF, R, double>;
+}
+
+const void *batch_ff_fn_rows(int rows)
+{
+    return rows <= 1 ? batch_ff_fn<1>() : rows <= 2 ? batch_ff_fn<2>() : rows <= 4 ? batch_ff_fn<4>() : batch_ff_fn<8>();
+}
+
+cudaError_t batch_launch_ff(const BatchBlocks &BB, const FF *G, const FF *d, const float *x, double *y,
+                            unsigned long long *counter, int grid, cudaStream_t st, const int *skip, int skip_stride)
+{
+    const size_t smem = layout3<float, FF>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh).total;
+    const int rows = (BB.max_block + kThreads - 1) / kThreads;
+    cudaError_t err = cudaFuncSetAttribute(batch_ff_fn_rows(rows), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    if (rows <= 1) hx3_batch_kernel<float, FF, 1, double><<<grid, kThreads, smem, st>>>(BB, G, d, x, y, counter, skip, skip_stride);
+    else if (rows <= 2) hx3_batch_kernel<float, FF, 2, double><<<grid, kThreads, smem, st>>>(BB, G, d, x, y, counter, skip, skip_stride);
+    else if (rows <= 4) hx3_batch_kernel<float, FF, 4, double><<<grid, kThreads, smem, st>>>(BB, G, d, x, y, counter, skip, skip_stride);
+    else hx3_batch_kernel<float, FF, 8, double><<<grid, kThreads, smem, st>>>(BB, G, d, x, y, counter, skip, skip_stride);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int batch_grid_ff(const BatchBlocks &BB)
+{
+    const size_t smem = layout3<float, FF>(BB.max_omega, BB.max_L, BB.max_H, BB.max_n, BB.max_block, BB.max_hh).total;
+    const void *fn = batch_ff_fn_rows((BB.max_block + kThreads - 1) / kThreads);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > BB.nblocks) g = BB.nblocks;
+    return (int)(g > 0 ? g : 1);
+}
 }  // namespace
 
 cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
                             unsigned long long *counter, int grid, cudaStream_t st, const int *skip, int skip_stride)
 {
     unsigned long long *ctr = counter;
+    if (precision == 2) {
+        if (!batch_ff_fits(BB) || !P.Gff || !P.dff || grid < 1) return cudaErrorNotSupported;
+        return batch_launch_ff(BB, reinterpret_cast<const FF *>(P.Gff), reinterpret_cast<const FF *>(P.dff),
+                               static_cast<const float *>(x), static_cast<double *>(y), ctr, grid, st, skip,
+                               skip_stride);
+    }
     if (precision == 0) return batch_launch_t<double, double>(BB, P.G64, P.d64, x, y, ctr, grid, st, skip, skip_stride);
     return batch_launch_t<float, float>(BB, P.G32, P.d32, x, y, ctr, grid, st, skip, skip_stride);
 }
 
 int hx_batch_grid(const BatchBlocks &BB, int precision)
 {
+    if (precision == 2) return batch_ff_fits(BB) ? batch_grid_ff(BB) : 0;
     return precision == 0 ? batch_grid_t<double, double>(BB) : batch_grid_t<float, float>(BB);
 }
 

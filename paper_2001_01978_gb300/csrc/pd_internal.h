@@ -299,6 +299,8 @@ struct HxProblem {
 // batched H*x: skip[p * skip_stride] != 0 passes over problem p (skip nullable).
 // counter: two zeroed device counters (next block, finished CTAs); the last CTA
 // returns both to zero, so no memset is needed between launches (graph-safe).
+// precision 2 (float-float rows, x float, y double) runs the batched variant-3
+// kernel whatever BB.variant says; hx_batch_grid(BB, 2) is 0 where it does not fit.
 cudaError_t hx_batch_launch(const BatchBlocks &BB, const HxProblem &P, int precision, const void *x, void *y,
                             unsigned long long *counter, int grid, cudaStream_t st, const int *skip, int skip_stride);
 int hx_batch_grid(const BatchBlocks &BB, int precision);
