@@ -140,6 +140,10 @@ int64_t pairdiag_dim(const pairdiag_t *h);
 int64_t pairdiag_nnz(const pairdiag_t *h);
 /* C(Omega,N), whether or not the handle is truncated. */
 int64_t pairdiag_full_dim(const pairdiag_t *h);
+/* The handle's number of orbits Omega (Eq. 2): the length of every per-orbit
+ * host array (pairdiag_set_start_weights, pairdiag_product_start_dev, the
+ * occupation numbers).  Host only, no device work; -1 for a null handle. */
+int pairdiag_omega(const pairdiag_t *h);
 
 /*
  * Basis states with indices [first, first+count) (Sec. 3.1, Table 1), written

@@ -944,6 +944,7 @@ int pairdiag_set_stream(pairdiag_t *h, void *stream)
 
 int64_t pairdiag_dim(const pairdiag_t *h) { return h ? h->dim : -1; }
 int64_t pairdiag_nnz(const pairdiag_t *h) { return h ? h->nnz : -1; }
+int pairdiag_omega(const pairdiag_t *h) { return h ? h->omega : -1; }
 
 int pairdiag_basis_dev(const pairdiag_t *h, int64_t first, int64_t count, uint64_t *out_dev)
 {

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "pairdiag_set_stream": (ctypes.c_int, [_H, _P]),
     "pairdiag_dim": (ctypes.c_int64, [_H]),
     "pairdiag_nnz": (ctypes.c_int64, [_H]),
+    "pairdiag_omega": (ctypes.c_int, [_H]),
     "pairdiag_basis_dev": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _P]),
     "pairdiag_basis": (ctypes.c_int, [_H, _P]),
     "pairdiag_rank_dev": (ctypes.c_int, [_H, _P, ctypes.c_int64, _P]),
@@ -198,6 +199,10 @@ def pairdiag_set_stream(h, stream) -> None:
 
 def pairdiag_dim(h) -> int:
     return int(lib().pairdiag_dim(h))
+
+
+def pairdiag_omega(h) -> int:
+    return int(lib().pairdiag_omega(h))
 
 
 def pairdiag_nnz(h) -> int:
@@ -395,10 +400,19 @@ def pairdiag_batch_ground_state(problems, tol: float, opt: pairdiag_options | No
     e0, status, iterations, converged, stalled, rel_residual, latency_ms and the
     call's status."""
     count = len(problems)
+    if count < 1:
+        raise ValueError("need at least one problem")
     om = np.array([p[0] for p in problems], dtype=np.int32)
     nn = np.array([p[1] for p in problems], dtype=np.int32)
-    e_all = np.ascontiguousarray(np.concatenate([np.asarray(p[2], dtype=np.float64).ravel() for p in problems]))
-    G_all = np.ascontiguousarray(np.concatenate([np.asarray(p[3], dtype=np.float64).ravel() for p in problems]))
+    es = [np.asarray(p[2], dtype=np.float64) for p in problems]
+    Gs = [np.asarray(p[3], dtype=np.float64) for p in problems]
+    # the library finds problem i's e and G at the running sums of omega and
+    # omega^2, so every shape must match its omega
+    for i, (o, e, G) in enumerate(zip(om, es, Gs)):
+        if e.shape != (o,) or G.shape != (o, o):
+            raise ValueError(f"problem {i}: e must be [omega] and G [omega, omega] (omega = {o})")
+    e_all = np.ascontiguousarray(np.concatenate([e.ravel() for e in es]))
+    G_all = np.ascontiguousarray(np.concatenate([G.ravel() for G in Gs]))
     e0 = np.empty(count)
     status = np.empty(count, dtype=np.int32)
     res = (pairdiag_batch_result * count)()
@@ -444,7 +458,11 @@ def pairdiag_odd_ground_state(omega: int, n_pairs: int, e, G, tol: float, block:
 def pairdiag_tridiag_lowest(h, alpha, beta):
     alpha = np.ascontiguousarray(alpha, dtype=np.float64)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
+    if alpha.ndim != 1 or beta.ndim != 1:
+        raise ValueError("alpha and beta must be 1-D")
     m = len(alpha)
+    if m < 1 or beta.size < m - 1:
+        raise ValueError(f"need m >= 1 diagonal entries and m - 1 off-diagonal ones (m = {m}, beta {beta.size})")
     theta = np.empty(2)
     s = np.empty(m)
     _check(lib().pairdiag_tridiag_lowest(h, m, _np_ptr(alpha), _np_ptr(beta) if m > 1 else None,
@@ -508,6 +526,8 @@ def pairdiag_mlp_get_params(m) -> np.ndarray:
 
 def pairdiag_mlp_set_params(m, theta) -> None:
     theta = np.ascontiguousarray(theta, dtype=np.float32)
+    if theta.size != pairdiag_mlp_num_params():
+        raise ValueError(f"theta must hold {pairdiag_mlp_num_params()} parameters, not {theta.size}")
     _check(lib().pairdiag_mlp_set_params(m, _np_ptr(theta)))
 
 
@@ -519,16 +539,29 @@ def pairdiag_mlp_features(omega: int, n_pairs: int, e, G) -> np.ndarray:
     return X
 
 
-def pairdiag_mlp_forward(m, X) -> np.ndarray:
+def _feature_rows(X, target=None):
+    """X as a contiguous float32 [rows, 16] array (and target as float32 [rows]):
+    the library reads rows * 16 and rows floats from them."""
     X = np.ascontiguousarray(X, dtype=np.float32)
+    if X.ndim != 2 or X.shape[1] != 16:
+        raise ValueError(f"X must be [rows, 16] feature rows, not {X.shape}")
+    if target is None:
+        return X
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    if t.shape != (len(X),):
+        raise ValueError(f"target must be [{len(X)}], not {t.shape}")
+    return X, t
+
+
+def pairdiag_mlp_forward(m, X) -> np.ndarray:
+    X = _feature_rows(X)
     out = np.empty(len(X), dtype=np.float32)
     _check(lib().pairdiag_mlp_forward(m, len(X), _np_ptr(X), _np_ptr(out)))
     return out
 
 
 def pairdiag_mlp_loss_grad(m, X, target):
-    X = np.ascontiguousarray(X, dtype=np.float32)
-    t = np.ascontiguousarray(target, dtype=np.float32)
+    X, t = _feature_rows(X, target)
     loss = ctypes.c_double()
     grad = np.empty(pairdiag_mlp_num_params(), dtype=np.float32)
     _check(lib().pairdiag_mlp_loss_grad(m, len(X), _np_ptr(X), _np_ptr(t), ctypes.byref(loss), _np_ptr(grad)))
@@ -545,8 +578,9 @@ def pairdiag_mlp_buffer(m, which: int, rows: int) -> np.ndarray:
 
 
 def pairdiag_mlp_train(m, X, target, steps: int, lr: float = 1e-3) -> np.ndarray:
-    X = np.ascontiguousarray(X, dtype=np.float32)
-    t = np.ascontiguousarray(target, dtype=np.float32)
+    X, t = _feature_rows(X, target)
+    if steps < 0:
+        raise ValueError("steps must be >= 0")
     hist = np.empty(steps, dtype=np.float64)
     _check(lib().pairdiag_mlp_train(m, len(X), _np_ptr(X), _np_ptr(t), steps, lr, _np_ptr(hist)))
     return hist
@@ -556,8 +590,20 @@ def pairdiag_set_mlp(h, m) -> None:
     _check(lib().pairdiag_set_mlp(h, m))
 
 
-def pairdiag_set_start_weights(h, w) -> None:
+def _orbit_weights(h, w):
+    """w as a contiguous float64 [omega] array for the handle's omega (the
+    library reads omega doubles from it)."""
     w = np.ascontiguousarray(w, dtype=np.float64)
+    omega = pairdiag_omega(h)
+    if omega < 1:
+        raise ValueError("not a valid handle")
+    if w.shape != (omega,):
+        raise ValueError(f"w must be [{omega}] (one weight per orbit), not {w.shape}")
+    return w
+
+
+def pairdiag_set_start_weights(h, w) -> None:
+    w = _orbit_weights(h, w)
     _check(lib().pairdiag_set_start_weights(h, _np_ptr(w)))
 
 
@@ -572,7 +618,7 @@ def pairdiag_product_fit(h, v, omega: int) -> np.ndarray:
 
 def pairdiag_product_start_dev(h, w, v) -> None:
     import torch
-    w = np.ascontiguousarray(w, dtype=np.float64)
+    w = _orbit_weights(h, w)
     if v.numel() < pairdiag_dim(h):
         raise ValueError("v must hold dim elements")
     _check(lib().pairdiag_product_start_dev(h, _np_ptr(w), _dev_ptr(v, torch.float64)))

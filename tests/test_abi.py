@@ -134,3 +134,35 @@ def test_multidot_wrappers_check_sizes_before_any_call():
     # sizes that fit pass the checks and stop at the device check
     with pytest.raises(TypeError, match="CUDA tensor"):
         pd.pairdiag_multidot_noalloc(Q, 8, 3, p, 8, torch.zeros(3, dtype=torch.float64))
+
+
+def test_host_array_wrappers_check_shapes_before_any_call(libpath):
+    """The library reads rows * 16 feature floats, num_params parameters, omega
+    weights per handle, omega and omega^2 inputs per batch problem and m - 1
+    off-diagonal entries from host pointers it cannot size, so the binding
+    rejects any other shape before a pointer is passed (a null network or
+    handle: nothing reaches a device)."""
+    import numpy as np
+    import paper_2001_01978_gb300 as pd
+    assert pd.pairdiag_omega(None) == -1
+    with pytest.raises(ValueError, match="theta must hold"):
+        pd.pairdiag_mlp_set_params(None, np.zeros(pd.pairdiag_mlp_num_params() - 1))
+    with pytest.raises(ValueError, match=r"\[rows, 16\]"):
+        pd.pairdiag_mlp_forward(None, np.zeros((5, 15)))
+    with pytest.raises(ValueError, match=r"\[rows, 16\]"):
+        pd.pairdiag_mlp_forward(None, np.zeros(16))
+    with pytest.raises(ValueError, match=r"target must be \[5\]"):
+        pd.pairdiag_mlp_loss_grad(None, np.zeros((5, 16)), np.zeros(4))
+    with pytest.raises(ValueError, match=r"target must be \[5\]"):
+        pd.pairdiag_mlp_train(None, np.zeros((5, 16)), np.zeros((5, 1)), 3)
+    with pytest.raises(ValueError, match="steps"):
+        pd.pairdiag_mlp_train(None, np.zeros((5, 16)), np.zeros(5), -1)
+    with pytest.raises(ValueError, match="not a valid handle"):
+        pd.pairdiag_set_start_weights(None, np.zeros(6))
+    with pytest.raises(ValueError, match="problem 1"):
+        pd.pairdiag_batch_ground_state([(6, 2, np.zeros(6), np.zeros((6, 6))),
+                                        (7, 3, np.zeros(7), np.zeros((6, 6)))], 1e-8)
+    with pytest.raises(ValueError, match="at least one problem"):
+        pd.pairdiag_batch_ground_state([], 1e-8)
+    with pytest.raises(ValueError, match="off-diagonal"):
+        pd.pairdiag_tridiag_lowest(None, np.zeros(4), np.zeros(2))

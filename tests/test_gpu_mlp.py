@@ -191,6 +191,12 @@ def test_product_fit_and_start_vs_numpy():
         w = pd.pairdiag_product_fit(s.h, vt, omega)
         assert np.max(np.abs(w - w_np)) < 1e-8 * max(1.0, np.max(np.abs(w_np)))
         out = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+        # one weight per orbit of the handle, checked before the library reads w
+        assert pd.pairdiag_omega(s.h) == omega
+        with pytest.raises(ValueError, match=r"w must be \[12\]"):
+            pd.pairdiag_product_start_dev(s.h, w[:-1], out)
+        with pytest.raises(ValueError, match=r"w must be \[12\]"):
+            pd.pairdiag_set_start_weights(s.h, np.r_[w, 0.0])
         pd.pairdiag_product_start_dev(s.h, w, out)
         ex = occ @ w
         assert np.allclose(out.cpu().numpy(), np.exp(ex - ex.max()), rtol=1e-12, atol=0)
