@@ -1342,7 +1342,8 @@ int pairdiag_multidot(pairdiag_t *h, int dtype, const void *Q_dev, int64_t ld, i
                       int64_t n, double *out)
 {
     if (!h || !Q_dev || !p_dev || !out) return fail(PD_EINVAL, "null argument");
-    if (m < 1 || m > kMaxWindow || n < 0 || (dtype != 0 && dtype != 1)) return fail(PD_EINVAL, "bad sizes");
+    if (m < 1 || m > kMaxWindow || n < 0 || ld < n || (dtype != 0 && dtype != 1))
+        return fail(PD_EINVAL, "bad sizes (need 1 <= m <= %d, 0 <= n <= ld, dtype 0 or 1)", kMaxWindow);
     PD_CUDA(multidot_launch(dtype, Q_dev, ld, m, p_dev, n, h->d_part, h->d_S->c1, h->st, nullptr,
                             &h->d_tk->vec_done));
     PD_CUDA(cudaMemcpyAsync(out, h->d_S->c1, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
