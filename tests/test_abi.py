@@ -166,3 +166,56 @@ def test_host_array_wrappers_check_shapes_before_any_call(libpath):
         pd.pairdiag_batch_ground_state([], 1e-8)
     with pytest.raises(ValueError, match="off-diagonal"):
         pd.pairdiag_tridiag_lowest(None, np.zeros(4), np.zeros(2))
+
+
+def test_create_and_batch_reject_invalid_input_before_any_device_call(libpath):
+    """Host-side fault injection: out-of-range sizes, non-finite or asymmetric
+    inputs and bad options make pairdiag_create and the batch return PD_EINVAL
+    (or PD_ENOTSUP for a form the batch does not run) before any CUDA call, so
+    these run on a machine without a GPU."""
+    import numpy as np
+    import paper_2001_01978_gb300 as pd
+    e = np.arange(6.0)
+    G = np.full((6, 6), -0.3)
+    asym = G + np.triu(np.full((6, 6), 1e-3), 1)
+    Gnan = G.copy()
+    Gnan[2, 3] = Gnan[3, 2] = np.nan
+    Ginf = G.copy()
+    Ginf[1, 1] = np.inf
+    opt = pd.pairdiag_default_options
+    bad_create = [
+        (6, 7, e, G, None),                      # more pairs than orbits
+        (6, -1, e, G, None),
+        (6, 2, e, asym, None),                   # G must be symmetric (reading r4)
+        (6, 2, np.r_[e[:5], np.nan], G, None),
+        (6, 2, e, Gnan, None),
+        (6, 2, e, Ginf, None),
+        (6, 2, e, G, opt(window=0)),
+        (6, 2, e, G, opt(window=65)),
+        (6, 2, e, G, opt(precision=2)),
+        (6, 2, e, G, opt(mode=2)),
+        (6, 2, e, G, opt(low_bits=40)),
+        (6, 2, e, G, opt(max_restarts=-1)),
+        (6, 2, e, G, opt(hx_variant=6)),
+        (6, 2, e, G, opt(start=5)),
+    ]
+    for om, n, ee, GG, o in bad_create:
+        with pytest.raises(pd.PairDiagError) as err:
+            pd.pairdiag_create(om, n, ee, GG, o)
+        assert err.value.code == pd.PD_EINVAL, (om, n, o)
+    ok = (6, 2, e, G)
+    bad_batch = [
+        ([ok, (6, 2, e, asym)], None, 1e-8, pd.PD_EINVAL),
+        ([ok, (6, 2, np.r_[e[:5], np.inf], G)], None, 1e-8, pd.PD_EINVAL),
+        ([ok, (6, 7, e, G)], None, 1e-8, pd.PD_EINVAL),
+        ([ok], None, -1.0, pd.PD_EINVAL),
+        ([ok], opt(window=0), 1e-8, pd.PD_EINVAL),
+        ([ok], opt(precision=2), 1e-8, pd.PD_EINVAL),
+        ([ok], opt(start=pd.PD_START_MLP), 1e-8, pd.PD_EINVAL),      # the learned start needs a network
+        ([ok], opt(start=pd.PD_START_FIRST), 1e-8, pd.PD_ENOTSUP),
+        ([ok], opt(mode=1), 1e-8, pd.PD_ENOTSUP),
+    ]
+    for probs, o, tol, code in bad_batch:
+        with pytest.raises(pd.PairDiagError) as err:
+            pd.pairdiag_batch_ground_state(probs, tol, o)
+        assert err.value.code == code, (o, tol, err.value.code)
