@@ -314,3 +314,62 @@ def test_ritz_residual_equals_beta_times_last_component(m):
     y = np.stack(Q[:m]).T @ S[:, 0]
     resid = np.linalg.norm(A @ y - w[0] * y)
     assert abs(resid - beta[-1] * abs(S[-1, 0])) <= 1e-10 * max(1.0, resid)
+
+
+def test_hellmann_feynman_occupations_and_couplings():
+    """The derivative of the ground-state energy of Eq. 2 with respect to a
+    parameter is the expectation value of the operator that multiplies it
+    (Hellmann-Feynman).  Central differences of the oracle's lowest eigenvalue
+    (numpy eigh of the oracle's matrix) must therefore equal, computed from
+    the basis bits and the ground state alone:
+      dE0/de_p  = 2 <n_p>  (the occupation number 2<S+_p S-_p> of Sec. 4.3),
+      dE0/dG_pp = <n_p>,
+      dE0/dG_pq = <P_p^+ P_q + P_q^+ P_p> for a symmetric change of G_pq and G_qp.
+    A missing factor 2 on e_p, a dropped G_pp or a hop weighted by the wrong
+    element of G fails one of these; the occupations also sum to 2N."""
+    omega, n = 8, 3
+    e, G = pd_inputs.separable_noise(omega, seed=4)
+    b = oracle.basis(omega, n)
+    index = {int(s): i for i, s in enumerate(b)}
+
+    def lowest(e_, G_):
+        return np.linalg.eigh(oracle.dense_matrix(omega, n, e_, G_))
+
+    w, V = lowest(e, G)
+    assert w[1] - w[0] > 1e-3                   # a non-degenerate ground state
+    v = V[:, 0]
+    bits = ((b[:, None] >> np.arange(omega, dtype=np.uint64)) & np.uint64(1)).astype(bool)
+    n_exp = np.array([np.sum(v[bits[:, p]] ** 2) for p in range(omega)])
+    assert abs(2 * n_exp.sum() - 2 * n) < 1e-12
+
+    h = 1e-4
+
+    def deriv(change):
+        ep, Gp = change(+h)
+        em, Gm = change(-h)
+        return (lowest(ep, Gp)[0][0] - lowest(em, Gm)[0][0]) / (2 * h)
+
+    def shift_e(p):
+        def f(t):
+            e2 = e.copy(); e2[p] += t
+            return e2, G
+        return f
+
+    def shift_G(p, q):
+        def f(t):
+            G2 = G.copy(); G2[p, q] += t
+            if p != q:
+                G2[q, p] += t
+            return e, G2
+        return f
+
+    for p in range(omega):
+        assert abs(deriv(shift_e(p)) - 2 * n_exp[p]) < 1e-7, p
+        assert abs(deriv(shift_G(p, p)) - n_exp[p]) < 1e-7, p
+    for p, q in [(0, 1), (2, 5), (3, 7), (6, 4)]:
+        hop = 0.0
+        for i, s in enumerate(b):
+            s = int(s)
+            if (s >> q) & 1 and not (s >> p) & 1:      # P_p^+ P_q: pair moves q -> p
+                hop += v[index[s ^ (1 << q) ^ (1 << p)]] * v[i]
+        assert abs(deriv(shift_G(p, q)) - 2 * hop) < 1e-7, (p, q)
