@@ -363,6 +363,7 @@ def run_ours(args):
     Bi = (omega + omega * omega) * 8
     Bo = dim * 8 + 8
     vec_host = torch.empty(dim, dtype=torch.float64, pin_memory=True).numpy()   # the caller's output buffer
+    barrier()                                  # replicas start their end-to-end solves together
     for _ in range(max(1, args.e2e_steps)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -375,7 +376,12 @@ def run_ours(args):
             r = s.ground_state(args.tol, want_vector=True, out=vec_host)   # E0 + eigenvector into pinned host memory
         e2e_s.append(time.perf_counter() - t0)
         e2e_hx.append(r["hx_products"])
-    e2e_value = sum(e2e_hx) * nnz / sum(e2e_s)
+    if dist is not None:
+        # whole job: the nonzeros of every replica over the slowest replica's time
+        e2e_ms_max, e2e_nnz_all = combine_ranks(1e3 * sum(e2e_s), float(sum(e2e_hx) * nnz), dist, "cuda")
+        e2e_value = e2e_nnz_all / (e2e_ms_max * 1e-3)
+    else:
+        e2e_value = sum(e2e_hx) * nnz / sum(e2e_s)
 
     # ---- the Omega=30 workload (dim 1.55e8) in the three forms: FP64 from a random
     # start, mixed from a random start, mixed from the learned start ----
@@ -385,7 +391,17 @@ def run_ours(args):
     # ---- ALU roof of the FP64 product (one FP64 FMA per nonzero) ----
     fma64 = pd.pairdiag_fma_peak(pd.PD_PREC_FP64, 5, stream)
 
+    def close_all():
+        for s_ in (mixed, mixed_rand, fp64):
+            if s_ is not None:
+                s_.close()
+        if ws is not None:
+            ws.close()
+        if dist is not None:
+            dist.destroy_process_group()
+
     if rank != 0:
+        close_all()
         return 0
 
     # ---- accuracy against the oracle's E0 (committed by tests/golden/make_golden.py) ----
@@ -406,14 +422,17 @@ def run_ours(args):
     avg_hx_s = (hx_ms / max(1, hx_executed)) * 1e-3
     achieved = alg_bytes / avg_hx_s / 1e9
     lb, hv = pd.pairdiag_tune_get(omega, n, pd.PD_PREC_MIXED)
-    if args.low_bits:
-        lb, hv = args.low_bits, args.hx_variant or 1
-    traffic = ncu_traffic(args.workload, "fp32", lb or 12, hv or 1)
+    if args.low_bits or args.hx_variant:
+        lb, hv = args.low_bits, args.hx_variant
+    # a zero (no recorded or requested value, e.g. --no-autotune) is left to the
+    # library's untuned default, which no traffic line describes
+    traffic = ncu_traffic(args.workload, "fp32", lb, hv) if lb and hv else None
+    kname = "H*x FP32 (low_bits %s, variant %s)" % (lb or "default", hv or "default")
     # achieved = algorithmic bytes (one gathered element per nonzero + the diagonal
     # read + the write) / time: an effective rate.  The DRAM bytes ncu counts are
     # far fewer (shared memory and L2 serve most gathers), so the kernel is bound
     # by instruction issue, not by DRAM; dram_gbs is the rate of those counted bytes.
-    roofline = {"kernel": "H*x FP32 (low_bits %d, variant %d)" % (lb or 12, hv or 1), "bound": "hbm",
+    roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": traffic, "achieved_is": "algorithmic bytes / time (effective)",
                 "dram_gbs": (traffic / avg_hx_s / 1e9) if traffic else None,
@@ -481,14 +500,7 @@ def run_ours(args):
         "clocks": clk,
     })
     print(json.dumps(line))
-    mixed.close()
-    for s_ in (mixed_rand, fp64):
-        if s_ is not None:
-            s_.close()
-    if ws is not None:
-        ws.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    close_all()
     return 0
 
 
